@@ -1,0 +1,358 @@
+"""Physics pins of the whole oracle step against what the paper fixes:
+conservation to round-off, relaxation to equilibrium, the homogeneous
+radiating sphere, the diffusion waves and the relativistic invariants
+(Sec. 4).  No GPU."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2003_02845_gb300 import workloads as W
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _run(orc, prob, n_steps, cfl=0.5, bg=0):
+    o = orc.Oracle(prob)
+    o.set_background(prob.backgrounds[bg])
+    o.set_f(prob.f0)
+    dt = o.max_dt(cfl)
+    for _ in range(n_steps):
+        o.step(dt)
+    return o, dt
+
+
+# --------------------------------------------------------------------------
+# Conservation on static backgrounds (number exactly by construction)
+# --------------------------------------------------------------------------
+def _scattering_only(prob, seed):
+    rng = np.random.default_rng(seed)
+    for bg in prob.backgrounds:
+        bg.kappa_a[:] = 0.0
+        bg.kappa_s[:] = rng.uniform(0.0, 3.0, bg.kappa_s.shape)
+    prob.f0 = rng.uniform(0.0, 1.0, prob.f0.shape)
+    return prob
+
+
+def test_conservation_static_flat_column(orc):
+    p = _scattering_only(W.homogeneous_sphere(n_r=12, kappa=0.0, n_e=3, n_mu=6, n_phi=4, dang=0.3), 1)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    N0, E0, _, _ = o.totals()
+    dt = o.max_dt(0.5)
+    for _ in range(40):
+        o.step(dt)
+    N, E, No, Eo = o.totals()
+    assert np.all(No > 1e-3 * N0)                      # something really left
+    assert np.allclose(N + No, N0, rtol=1e-13, atol=0)
+    assert np.allclose(E + Eo, E0, rtol=1e-13, atol=0)
+
+
+def test_conservation_static_flat_2d(orc):
+    p = W.random_2d(11, n_r=6, n_theta=5, n_e=3, n_mu=4, n_phi=6, n_s=1)
+    for bg in p.backgrounds:
+        bg.v[:] = 0.0
+        bg.alpha[:] = 1.0
+        bg.phi[:] = 1.0
+    p = _scattering_only(p, 2)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    N0, E0, _, _ = o.totals()
+    dt = o.max_dt(0.5)
+    for _ in range(30):
+        o.step(dt)
+    N, E, No, Eo = o.totals()
+    assert np.allclose(N + No, N0, rtol=1e-13, atol=0)
+    assert np.allclose(E + Eo, E0, rtol=1e-13, atol=0)
+
+
+def test_conservation_static_curved_moving(orc):
+    # static lapse/conformal factor and a static velocity field: number is
+    # conserved exactly; with v = 0 the energy at infinity too (the kick
+    # conserves alpha*eps and the energy weights conserve eps), as long as no
+    # energy is clamped at the ends of a wide group grid
+    # 24 groups, content only in the middle 4; a step shifts content by at
+    # most two groups (remap into the face frame, then deposit), so 5 steps
+    # never reach the clamped ends
+    p = W.random_column(5, n_r=10, n_e=24, n_mu=6, n_phi=4, n_s=1, moving=True, gr=True)
+    p.eps_edges = np.geomspace(1e-3, 1e4, 25)
+    p = _scattering_only(p, 3)
+    keep = np.zeros(24, bool)
+    keep[10:14] = True
+    p.f0[:, :, ~keep, :] = 0.0
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    N0, _, _, _ = o.totals()
+    dt = o.max_dt(0.5)
+    for _ in range(5):
+        o.step(dt)
+    N, E, No, Eo = o.totals()
+    assert np.allclose(N + No, N0, rtol=1e-13, atol=0)
+
+    p.backgrounds[0].v[:] = 0.0
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    N0, E0, _, _ = o.totals()
+    for _ in range(5):
+        o.step(dt)
+    N, E, No, Eo = o.totals()
+    assert o.tir_count() > 0                          # reflection branch exercised
+    assert np.allclose(N + No, N0, rtol=1e-13, atol=0)
+    assert np.allclose(E + Eo, E0, rtol=1e-13, atol=0)
+
+
+def test_time_remap_conserves_number(orc):
+    # alternating moving/curved backgrounds with no transport change
+    p = W.random_column(7, n_r=6, n_e=5, n_mu=4, n_phi=4, n_s=2)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    N0 = o.totals()[0]
+    o.set_background(p.backgrounds[1])
+    o.step_zones(1e-30, [0])        # applies the pending time remap to every zone
+    N1 = o.totals()[0]
+    assert np.allclose(N1, N0, rtol=1e-13)
+
+
+def test_time_remap_identity_for_same_background(orc):
+    p = W.random_column(8, n_r=5, n_e=3, n_mu=4, n_phi=4, n_s=1)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    o.set_background(p.backgrounds[0])
+    f0 = o.get_f()
+    o.step_zones(1e-30, [0])
+    assert np.allclose(o.get_f(), f0, rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Relaxation to f_eq at high opacity
+# --------------------------------------------------------------------------
+def test_relaxation_to_equilibrium(orc):
+    p = W.random_column(9, n_r=8, n_e=4, n_mu=4, n_phi=4, n_s=2, moving=False, gr=False)
+    o0 = orc.Oracle(p)
+    o0.set_background(p.backgrounds[0])
+    dt = o0.max_dt(0.5)
+    for bg in p.backgrounds:
+        bg.kappa_a[:] = 1e7 / dt
+        bg.kappa_s[:] = 3e6 / dt
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    for _ in range(4):
+        o.step(dt)
+    f = o.get_f()
+    feq = p.backgrounds[0].f_eq[..., None]
+    assert np.max(np.abs(f - feq) / feq) < 1e-5
+
+
+# --------------------------------------------------------------------------
+# Courant limit closed form
+# --------------------------------------------------------------------------
+def test_max_dt_slab_closed_form(orc):
+    p = W.slab_diffusion(kappa_s=1.0, dz=0.05, z_max=0.5, n_mu=6)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    mu, _ = orc.gauss_legendre(6)
+    assert math.isclose(o.max_dt(0.5), 0.5 * 0.05 / mu[-1], rel_tol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Subset stepping used for sampled parity at full size
+# --------------------------------------------------------------------------
+def test_step_zones_matches_full_step(orc):
+    p = W.random_2d(12, n_r=6, n_theta=4, n_e=3, n_mu=4, n_phi=4, n_s=2)
+    oa = orc.Oracle(p)
+    oa.set_background(p.backgrounds[0])
+    oa.set_f(p.f0)
+    oa.set_background(p.backgrounds[1])
+    dt = oa.max_dt(0.5)
+    ob = orc.Oracle(p)
+    ob.set_background(p.backgrounds[0])
+    ob.set_f(p.f0)
+    ob.set_background(p.backgrounds[1])
+    zones = [0, 5, 7, 23]
+    out = ob.step_zones(dt, zones)
+    oa.step(dt)
+    fa = oa.get_f()
+    assert np.array_equal(out[:, zones], fa[:, zones])
+
+
+# --------------------------------------------------------------------------
+# Homogeneous radiating sphere (Sec. 4.1)
+# --------------------------------------------------------------------------
+def sphere_exact(r, R=1.0, ka=4.0, n=4000):
+    mu = (np.arange(n) + 0.5) / n * 2 - 1
+    g = np.sqrt(np.clip(1 - (r / R) ** 2 * (1 - mu ** 2), 0, None))
+    if r < R:
+        s = r * mu + R * g
+    else:
+        s = np.where(mu >= math.sqrt(max(0.0, 1 - (R / r) ** 2)), 2 * R * g, 0.0)
+    f = 1 - np.exp(-ka * s)
+    return np.sum(mu * f) / np.sum(f), np.sum(mu * mu * f) / np.sum(f)
+
+
+def test_homogeneous_sphere_steady_state(orc):
+    tau = GOLDEN["radiating_sphere_setup"]["tau_low"]
+    p = W.homogeneous_sphere(n_r=24, kappa=tau, n_e=1, n_mu=16, n_phi=4, dang=0.25)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    dt = o.max_dt(0.5)
+    for _ in range(int(6.0 / dt)):
+        o.step(dt)
+    J, H, K = o.jhk()
+    rc = 0.5 * (p.r_edges[1:] + p.r_edges[:-1])
+    m = (rc > 1.0) & (rc < 2.0)
+    ex = np.array([sphere_exact(r, ka=tau) for r in rc[m]])
+    dH = np.sqrt(np.mean((H[0, m, 0] / J[0, m, 0] - ex[:, 0]) ** 2))
+    dK = np.sqrt(np.mean((K[0, m, 0] / J[0, m, 0] - ex[:, 1]) ** 2))
+    ref = GOLDEN["radiating_sphere_msd_boltzmann"]
+    assert dH < ref["delta_H_over_J"] and dK < ref["delta_K_over_J"]
+
+
+def test_free_streaming_outside_sphere_keeps_number(orc):
+    # the vacuum region only moves number around: outflow + content + the
+    # collision exchange of the last steps balance
+    p = W.homogeneous_sphere(n_r=16, kappa=4.0, n_e=2, n_mu=8, n_phi=4, dang=0.25)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    dt = o.max_dt(0.5)
+    vol = o.grid()["vol"]
+    Nprev = o.totals()[0][0]
+    Noprev = 0.0
+    for _ in range(30):
+        o.step(dt)
+        N, _, No, _ = o.totals()
+        dN = o.moments()[0][0]
+        src = np.sum(dN * vol) * dt
+        assert math.isclose(N[0] - Nprev + (No[0] - Noprev), src, rel_tol=1e-12, abs_tol=1e-18)
+        Nprev, Noprev = N[0], No[0]
+
+
+# --------------------------------------------------------------------------
+# Diffusion waves (Sec. 4.3)
+# --------------------------------------------------------------------------
+def test_planar_diffusion_wave(orc):
+    cfg = GOLDEN["diffusion_wave_planar"]
+    ks, t = cfg["kappa_s"], cfg["t0"]
+    p = W.slab_diffusion(kappa_s=ks, dz=cfg["dz"], t0=t)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    dt = o.max_dt(0.5)
+    zc = 0.5 * (p.r_edges[1:] + p.r_edges[:-1])
+    g = o.grid()
+    sc = 4 * math.pi * g["eps_c"][0] * g["dgam"][0]
+    for ts in cfg["t_samples"]:
+        n = int(round((ts - t) / dt))
+        for _ in range(n):
+            o.step(dt)
+        t += n * dt
+        J, H, _ = o.jhk()
+        E, F = 4 * math.pi * J[0, :, 0] / sc, 4 * math.pi * H[0, :, 0] / sc
+        Eex = math.sqrt(ks / t) * np.exp(-3 * ks * zc ** 2 / (4 * t))
+        Fex = zc / (2 * t) * Eex
+        assert np.linalg.norm(E - Eex) / np.linalg.norm(Eex) < 0.01
+        assert np.linalg.norm(F - Fex) / np.linalg.norm(Fex) < 0.02
+
+
+def test_spherical_diffusion_wave(orc):
+    cfg = GOLDEN["diffusion_wave_spherical"]
+    ks = cfg["kappa_s"]
+    nr = 40
+    p = W.homogeneous_sphere(n_r=nr, r_max=1.0, kappa=0.0, n_e=1, n_mu=8, n_phi=4, dang=0.25)
+    rc = 0.5 * (p.r_edges[1:] + p.r_edges[:-1])
+    p.backgrounds[0].kappa_s[:] = ks
+    E0 = ks ** 1.5 * np.exp(-3 * ks * rc ** 2 / 4)
+    p.f0 = E0[None, :, None, None] * np.ones((1, nr, 1, 32))
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    dt = o.max_dt(0.5)
+    g = o.grid()
+    sc = 4 * math.pi * g["eps_c"][0] * g["dgam"][0]
+    t = cfg["t0"]
+    ts = cfg["t_samples"][0]
+    n = int(round((ts - t) / dt))
+    for _ in range(n):
+        o.step(dt)
+    t += n * dt
+    J, H, _ = o.jhk()
+    E, F = 4 * math.pi * J[0, :, 0] / sc, 4 * math.pi * H[0, :, 0] / sc
+    Eex = (ks / t) ** 1.5 * np.exp(-3 * ks * rc ** 2 / (4 * t))
+    Fex = rc / (2 * t) * Eex
+    m = rc < 0.35                    # bulk of the wave
+    assert np.linalg.norm(E[m] - Eex[m]) / np.linalg.norm(Eex[m]) < 0.05
+    m2 = m & (rc > 0.05)             # away from the grid singularity at r = 0
+    assert np.linalg.norm(F[m2] - Fex[m2]) / np.linalg.norm(Fex[m2]) < 0.05
+
+
+# --------------------------------------------------------------------------
+# Relativistic radiating spheres (Sec. 4.2): invariants in vacuum
+# --------------------------------------------------------------------------
+def _relativistic_sphere(nr, lapse, shock):
+    r_edges = np.geomspace(0.5, 8.0, nr + 1)
+    rc = 0.5 * (r_edges[1:] + r_edges[:-1])
+    n_e = 12
+    p = W.homogeneous_sphere(n_r=nr, n_e=n_e, n_mu=8, n_phi=4, dang=math.log(16) / nr)
+    p.r_edges = r_edges
+    p.eps_edges = np.geomspace(4.0, 240.0, n_e + 1)
+    bg = p.backgrounds[0]
+    bg.kappa_a[:] = 0.0
+    bg.kappa_a[0, rc < 1.0, :] = 100.0
+    em = np.sqrt(p.eps_edges[1:] * p.eps_edges[:-1])
+    bg.f_eq[0] = 1.0 / (np.exp(em / 15.0) + 1.0)
+    cfg = GOLDEN["relativistic_sphere_lapse"]
+    if lapse:
+        rl = cfg["r_lapse_over_r_sphere"]
+        a0 = cfg["alpha_core"]
+        bg.alpha = np.where(rc < rl, a0, a0 + (1 - a0) * (1 - rl / rc))
+        bg.phi = bg.alpha ** -0.5
+    if shock:
+        vs = GOLDEN["relativistic_sphere_shock"]["v_shock"]
+        bg.v[:, 0] = np.where(rc < 3.0, 0.0, np.where(rc < 3.5, vs * (rc - 3.0) / 0.5, vs * (3.5 / rc) ** 2))
+    p.f0 = np.zeros((1, nr, n_e, 32))
+    return p, rc
+
+
+def _invariants(o, p, rc):
+    J, H, K = o.jhk()
+    g = o.grid()
+    bg = p.backgrounds[0]
+    Hs = H[0].sum(1)
+    Hn = (H[0] / g["eps_c"][None, :]).sum(1)
+    vr = bg.v[:, 0]
+    gam = 1 / np.sqrt(1 - vr ** 2)
+    L = 16 * math.pi * bg.alpha ** 2 * bg.phi ** 4 * Hs * rc ** 2 * (1 + vr) / (1 - vr)
+    eav = gam * (1 + vr) * bg.alpha * Hs / Hn
+    return L, eav
+
+
+def test_gravitational_redshift_invariant(orc):
+    p, rc = _relativistic_sphere(32, lapse=True, shock=False)
+    o, dt = _run(orc, p, 0)
+    for _ in range(int(30.0 / dt)):
+        o.step(dt)
+    L, eav = _invariants(o, p, rc)
+    m = rc > 1.5
+    assert (eav[m].max() - eav[m].min()) / eav[m].mean() < 0.02
+
+
+@pytest.mark.slow
+def test_doppler_invariants(orc):
+    p, rc = _relativistic_sphere(32, lapse=False, shock=True)
+    o, dt = _run(orc, p, 0)
+    for _ in range(int(20.0 / dt)):
+        o.step(dt)
+    L, eav = _invariants(o, p, rc)
+    m = (rc > 1.5) & (rc < 7.5)
+    assert (eav[m].max() - eav[m].min()) / eav[m].mean() < 0.05
+    assert (L[m].max() - L[m].min()) / L[m].mean() < 0.10

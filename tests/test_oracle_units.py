@@ -1,0 +1,374 @@
+"""Pins of the oracle's building blocks against closed forms, textbook
+special cases and independent formulations (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+
+# --------------------------------------------------------------------------
+# Momentum grid (Sec. 3.1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 8, 9, 16, 17, 32])
+def test_gauss_legendre_matches_textbook(orc, n):
+    x, w = orc.gauss_legendre(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.allclose(x, xr, atol=2e-15, rtol=0)
+    assert np.allclose(w, wr, atol=2e-15, rtol=0)
+    # exact mirror symmetry is relied on by the reflecting wall
+    assert np.array_equal(x, -x[::-1])
+    assert np.array_equal(w, w[::-1])
+
+
+# --------------------------------------------------------------------------
+# Frames and the geometric rotation G (Sec. 3.2.1)
+# --------------------------------------------------------------------------
+def rodrigues(k, beta):
+    """Rotation of components about unit axis k by angle beta (Sec. 3.2.1),
+    as a matrix acting on the (r, theta, phi) components."""
+    k = np.asarray(k, float)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return math.cos(beta) * np.eye(3) + math.sin(beta) * K + (1 - math.cos(beta)) * np.outer(k, k)
+
+
+def test_triad_orthonormal(orc):
+    for th, ph in [(0.3, 0.1), (1.2, -0.4), (math.pi / 2, 0.0), (2.9, 2.0)]:
+        E = orc.triad(th, ph)
+        assert np.allclose(E.T @ E, np.eye(3), atol=1e-15)
+        assert np.isclose(np.linalg.det(E), 1.0)
+
+
+@pytest.mark.parametrize("th,d", [(0.7, 0.05), (1.5, 0.125), (2.6, 0.3)])
+def test_rotation_theta_step_is_rodrigues_about_phi_hat(orc, th, d):
+    # a theta step by d: rotation by -d about k = (0,0,1) in (r,theta,phi) components
+    G = orc.rotation(th, 0.0, th + d, 0.0)
+    assert np.allclose(G, rodrigues([0, 0, 1], -d), atol=2e-15)
+    assert np.allclose(G @ G.T, np.eye(3), atol=2e-15)
+
+
+@pytest.mark.parametrize("th,d", [(0.7, 0.05), (1.5, 0.125), (2.6, 0.3)])
+def test_rotation_phi_step_is_rodrigues_about_z(orc, th, d):
+    # a phi step: rotation by -d about the polar axis z, whose components in
+    # the local (r, theta, phi) triad are (cos th, -sin th, 0)
+    G = orc.rotation(th, 0.0, th, d)
+    assert np.allclose(G, rodrigues([math.cos(th), -math.sin(th), 0.0], -d), atol=2e-15)
+
+
+# --------------------------------------------------------------------------
+# Lorentz boost (Sec. 3.2.2)
+# --------------------------------------------------------------------------
+def test_boost_inverse_and_null(orc):
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        v = rng.uniform(-0.3, 0.3, 3)
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        u = np.r_[1.0, n]
+        ue = orc.boost(v, +1, u)
+        assert abs(ue[0] ** 2 - ue[1:] @ ue[1:]) < 1e-14
+        back = orc.boost(v, -1, ue)
+        assert np.allclose(back, u, atol=1e-14)
+
+
+def test_boost_collinear_doppler_and_aberration(orc):
+    for v in (0.1, -0.2, 0.45):
+        g = 1 / math.sqrt(1 - v * v)
+        for mu in (-0.9, -0.3, 0.0, 0.5, 0.99):
+            s = math.sqrt(1 - mu * mu)
+            ue = orc.boost([v, 0, 0], +1, [1.0, mu, s, 0.0])
+            assert math.isclose(ue[0], g * (1 + v * mu), rel_tol=1e-14)               # Doppler factor
+            assert math.isclose(ue[1] / ue[0], (mu + v) / (1 + v * mu), abs_tol=1e-14)  # aberration
+            assert math.isclose(ue[2], s, rel_tol=1e-14)                              # transverse unchanged
+
+
+def test_boost_zero_velocity_is_identity(orc):
+    u = np.array([1.0, 0.6, 0.64, 0.48])
+    assert np.array_equal(orc.boost([0, 0, 0], +1, u), u)
+
+
+# --------------------------------------------------------------------------
+# Hamiltonian kick (Sec. 3.2.4)
+# --------------------------------------------------------------------------
+def kick_from_quadratic(axis, a_s, c_s, a_d, c_d, u):
+    """The paper's quadratic for delta, written in covariant coordinate
+    components of the CFC metric with zero shift: g^00 = -1/alpha^2,
+    g^ij = phi^-4 delta^ij; u_0 = -alpha e, u_i = phi^2 p_i."""
+    e, p = u[0], np.array(u[1:])
+    cov = np.r_[-a_s * e, c_s ** 2 * p]
+    gs = np.array([-1 / a_s ** 2, c_s ** -4, c_s ** -4, c_s ** -4])
+    gd = np.array([-1 / a_d ** 2, c_d ** -4, c_d ** -4, c_d ** -4])
+    i = 1 + axis
+    A = gd[i]
+    B = gd[i] * cov[i]                    # g^{mu i}_dst u_mu (diagonal metric)
+    Cc = np.sum((gd - gs) * cov * cov)    # delta g^{mu nu} u_mu u_nu
+    disc = B * B - A * Cc
+    assert disc >= 0
+    sgn = 1.0 if cov[i] >= 0 else -1.0
+    delta = (-B + sgn * math.sqrt(disc)) / A
+    cd = cov.copy()
+    cd[i] += delta
+    return np.r_[-cd[0] / a_d, cd[1:] / c_d ** 2]
+
+
+def test_kick_matches_paper_quadratic(orc):
+    rng = np.random.default_rng(1)
+    n_checked = 0
+    for _ in range(200):
+        axis = int(rng.integers(0, 3))
+        a_s, a_d = rng.uniform(0.6, 1.0, 2)
+        c_s, c_d = rng.uniform(1.0, 1.3, 2)
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        u = np.r_[1.0, n]
+        out, tir = orc.kick(axis, a_s, c_s, a_d, c_d, u)
+        if tir:
+            continue
+        ref = kick_from_quadratic(axis, a_s, c_s, a_d, c_d, u)
+        assert np.allclose(out, ref, atol=1e-13)
+        n_checked += 1
+    assert n_checked > 100
+
+
+def test_kick_conservation_and_null(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        axis = int(rng.integers(0, 3))
+        a_s, a_d = rng.uniform(0.5, 1.0, 2)
+        c_s, c_d = rng.uniform(1.0, 1.4, 2)
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        u = np.r_[1.0, n]
+        out, tir = orc.kick(axis, a_s, c_s, a_d, c_d, u)
+        # null in the destination metric and energy at infinity conserved
+        assert abs(out[0] ** 2 - out[1:] @ out[1:]) < 1e-13
+        assert math.isclose(a_d * out[0], a_s * u[0], rel_tol=1e-14)
+        t = [k for k in range(3) if k != axis]
+        if not tir:
+            # tangential covariant components conserved, normal sign kept
+            assert np.allclose(c_d ** 2 * out[1:][t], c_s ** 2 * u[1:][t], atol=1e-14)
+            assert out[1 + axis] * u[1 + axis] >= 0
+        else:
+            assert out[1 + axis] == 0.0
+
+
+def test_kick_identity_and_continuity(orc):
+    u = np.array([1.0, 0.3, -0.5, math.sqrt(1 - 0.09 - 0.25)])
+    out, tir = orc.kick(0, 0.8, 1.1, 0.8, 1.1, u)
+    assert not tir and np.allclose(out, u, atol=1e-16)
+    # delta -> 0 as delta g -> 0
+    prev = None
+    for eps in (1e-2, 1e-4, 1e-6):
+        out, _ = orc.kick(0, 0.8, 1.1, 0.8 * (1 + eps), 1.1 * (1 - eps), u)
+        d = np.abs(out - u).max()
+        if prev is not None:
+            assert d < prev * 0.05
+        prev = d
+
+
+def test_kick_reflection_branch_is_continuous(orc):
+    # outward grazing ray climbing out of a well: find the threshold and
+    # check both branches agree there
+    a_s, a_d = 0.80, 0.84
+    c_s, c_d = a_s ** -0.5, a_d ** -0.5
+    def out_for(mu):
+        s = math.sqrt(1 - mu * mu)
+        return orc.kick(0, a_s, c_s, a_d, c_d, [1.0, mu, s, 0.0])
+    lo, hi = 1e-6, 0.9          # lo reflects, hi passes
+    assert out_for(lo)[1] == 1 and out_for(hi)[1] == 0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if out_for(mid)[1]:
+            lo = mid
+        else:
+            hi = mid
+    o1, o2 = out_for(lo)[0], out_for(hi)[0]
+    assert np.allclose(o1, o2, atol=1e-6)
+
+
+def test_time_kick_conserves_spatial_covariant(orc):
+    u = np.array([1.0, 0.6, 0.0, 0.8])
+    out, tir = orc.kick(orc.KICK_TIME, 0.7, 1.2, 0.75, 1.15, u)
+    assert not tir
+    assert np.allclose(1.15 ** 2 * out[1:], 1.2 ** 2 * u[1:], atol=1e-15)
+    assert math.isclose(out[0], np.linalg.norm(out[1:]), rel_tol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Transformation chain (Eq. transformchain)
+# --------------------------------------------------------------------------
+def test_chain_identity(orc):
+    v = [0.1, -0.05, 0.02]
+    for mu, ph in [(0.3, 0.4), (-0.8, 2.0), (0.95, 5.5)]:
+        s = math.sqrt(1 - mu * mu)
+        n = [mu, s * math.cos(ph), s * math.sin(ph)]
+        rho, mus, phs, tir = orc.chain(v, 0.9, 1.05, v, 0.9, 1.05, np.eye(3), orc.KICK_R, n)
+        assert math.isclose(rho, 1.0, rel_tol=1e-14)
+        assert math.isclose(mus, mu, abs_tol=1e-14)
+        assert math.isclose(phs, ph, abs_tol=1e-12)
+
+
+def test_chain_radial_boost_doppler(orc):
+    # comoving frame of the source at rest, destination fluid moving with v:
+    # the destination comoving energy and direction follow the textbook
+    # Doppler shift gamma (1 - v mu) and aberration (mu - v)/(1 - v mu)
+    for v in (0.05, -0.2, 0.3):
+        g = 1 / math.sqrt(1 - v * v)
+        for mu in (-0.7, 0.1, 0.9):
+            s = math.sqrt(1 - mu * mu)
+            rho, mus, phs, _ = orc.chain([0, 0, 0], 1, 1, [v, 0, 0], 1, 1, np.eye(3),
+                                         orc.KICK_R, [mu, s, 0.0])
+            assert math.isclose(rho, g * (1 - v * mu), rel_tol=1e-14)
+            assert math.isclose(mus, (mu - v) / (1 - v * mu), abs_tol=1e-14)
+
+
+def test_chain_static_redshift(orc):
+    # static lapse step: comoving = Eulerian, energy ratio alpha_src/alpha_dst
+    for mu in (0.2, 0.7, -0.5):
+        s = math.sqrt(1 - mu * mu)
+        rho, mus, _, tir = orc.chain([0, 0, 0], 0.7, 0.7 ** -0.5, [0, 0, 0], 0.6, 0.6 ** -0.5,
+                                     np.eye(3), orc.KICK_R, [mu, s, 0])
+        assert not tir
+        assert math.isclose(rho, 0.7 / 0.6, rel_tol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Interpolation weights (Sec. 3.2: number, direction and energy conserved)
+# --------------------------------------------------------------------------
+def test_weights_reproduce_target(orc):
+    rng = np.random.default_rng(3)
+    mu_nodes, _ = orc.gauss_legendre(8)
+    R = 1.4
+    for _ in range(300):
+        mus = rng.uniform(mu_nodes[0], mu_nodes[-1])
+        j, w = orc.weights_mu(mus, mu_nodes)
+        assert 0 <= w <= 1
+        assert math.isclose((1 - w) * mu_nodes[j] + w * mu_nodes[j + 1], mus, abs_tol=1e-15)
+        rho = math.exp(rng.uniform(-1, 1))
+        m, w = orc.weights_eps(rho, R)
+        for eps_i in (1.0, 7.3):
+            tgt = (1 - w) * eps_i * R ** m + w * eps_i * R ** (m + 1)
+            assert math.isclose(tgt, rho * eps_i, rel_tol=1e-14)
+        nphi = int(rng.integers(2, 12))
+        phis = rng.uniform(0, 2 * math.pi)
+        k, w = orc.weights_phi(phis, nphi)
+        dP = 2 * math.pi / nphi
+        pl = (k + 0.5) * dP
+        pr = pl + dP
+        tgt = ((1 - w) * pl + w * pr) % (2 * math.pi)
+        assert math.isclose(tgt, phis, abs_tol=1e-13) or math.isclose(abs(tgt - phis), 2 * math.pi, abs_tol=1e-13)
+
+
+def test_weights_clamp_outside(orc):
+    mu_nodes, _ = orc.gauss_legendre(6)
+    assert orc.weights_mu(0.9999, mu_nodes) == (4, 1.0)
+    assert orc.weights_mu(-0.9999, mu_nodes) == (0, 0.0)
+
+
+# --------------------------------------------------------------------------
+# Implicit collision solve (Sec. 3.5)
+# --------------------------------------------------------------------------
+def backward_euler_matrix(tau, ka, ks, dOm):
+    # (1 + (ka+ks) tau_b) f_b - ks tau_b / 4pi sum_b' dOm_b' f_b' = rhs_b
+    n = len(tau)
+    M = np.diag(1 + (ka + ks) * tau)
+    M -= (ks * tau / (4 * math.pi))[:, None] * dOm[None, :]
+    return M
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_collision_matches_dense_solve(orc, seed):
+    rng = np.random.default_rng(seed)
+    n = 24
+    mu, dmu = orc.gauss_legendre(6)
+    dOm = np.repeat(dmu, 4) * (2 * math.pi / 4)
+    tau = rng.uniform(0.1, 5.0, n) * 10 ** rng.uniform(-2, 4)
+    ka, ks = rng.uniform(0, 3), rng.uniform(0, 5)
+    r = rng.uniform(0, 1, n)
+    f = orc.collision_row(r, tau, ka, ks, dOm)
+    ref = np.linalg.solve(backward_euler_matrix(tau, ka, ks, dOm), r)
+    assert np.allclose(f, ref, rtol=1e-12, atol=0)
+
+
+def test_collision_fixed_point_and_conservation(orc):
+    rng = np.random.default_rng(7)
+    mu, dmu = orc.gauss_legendre(8)
+    dOm = np.repeat(dmu, 5) * (2 * math.pi / 5)
+    u0 = rng.uniform(0.8, 1.2, 40)
+    dt, alpha = 0.3, 0.9
+    tau = alpha * dt / u0
+    # f = f_eq is a fixed point
+    feq = 0.37
+    f = orc.collision_row(feq + tau * 2.0 * feq, tau, 2.0, 5.0, dOm)
+    assert np.allclose(f, feq, rtol=1e-15)
+    # ka = 0: sum dOm u0 f conserved (isotropic scattering keeps lab content)
+    fs = rng.uniform(0, 1, 40)
+    f = orc.collision_row(fs, tau, 0.0, 7.0, dOm)
+    assert math.isclose(np.sum(dOm * u0 * f), np.sum(dOm * u0 * fs), rel_tol=1e-14)
+
+
+def test_collision_uniform_tau_closed_form(orc):
+    # for uniform tau the exact solution is [r + ks tau J_r/(1 + ka tau)] / D
+    # with J_r = 1/4pi sum dOm r  (the printed formula with its denominator fixed)
+    mu, dmu = orc.gauss_legendre(4)
+    dOm = np.repeat(dmu, 3) * (2 * math.pi / 3)
+    r = np.linspace(0.1, 0.9, 12)
+    tau, ka, ks = 0.7, 1.3, 2.1
+    f = orc.collision_row(r, np.full(12, tau), ka, ks, dOm)
+    Jr = np.sum(dOm * r) / (4 * math.pi)
+    ref = (r + ks * tau * Jr / (1 + ka * tau)) / (1 + (ka + ks) * tau)
+    assert np.allclose(f, ref, rtol=1e-14)
+
+
+def test_mc_limiter_textbook(orc):
+    assert orc.mc(1.0, 3.0) == 2.0
+    assert orc.mc(3.0, 1.0) == 2.0
+    assert orc.mc(1.0, -1.0) == 0.0
+    assert orc.mc(-2.0, -1.0) == -1.5
+    assert orc.mc(0.0, 5.0) == 0.0
+    assert orc.mc(1.0, 1.2) == 1.1
+
+
+# --------------------------------------------------------------------------
+# Geometry (Sec. 3.1): flat-faced cells
+# --------------------------------------------------------------------------
+def trapezoid(a, b, h):
+    return 0.5 * (a + b) * h
+
+
+@pytest.mark.parametrize("th0,th1,dph", [(0.2, 0.35, 0.1), (1.4, 1.6, 0.125), (2.9, math.pi, 0.05)])
+def test_face_areas_closed_form(orc, th0, th1, dph):
+    r0, r1 = 1.3, 1.9
+    # phi face: difference of two triangles from the origin
+    assert math.isclose(orc.face_area_ph(r0, r1, th0, th1, 0.3), 0.5 * math.sin(th1 - th0) * (r1 ** 2 - r0 ** 2), rel_tol=1e-13)
+    # r face: isosceles trapezoid of chords 2 r sin(th) sin(dph/2)
+    c = math.cos(dph / 2)
+    h = r1 * math.hypot(c * (math.sin(th1) - math.sin(th0)), math.cos(th1) - math.cos(th0))
+    ref = trapezoid(2 * r1 * math.sin(th0) * math.sin(dph / 2), 2 * r1 * math.sin(th1) * math.sin(dph / 2), h)
+    assert math.isclose(orc.face_area_r(r1, th0, th1, dph), ref, rel_tol=1e-12)
+    # theta face: trapezoid of chords at r0 and r1 along the bisector
+    hb = (r1 - r0) * math.hypot(math.sin(th0) * c, math.cos(th0))
+    ref = trapezoid(2 * r0 * math.sin(th0) * math.sin(dph / 2), 2 * r1 * math.sin(th0) * math.sin(dph / 2), hb)
+    assert math.isclose(orc.face_area_th(r0, r1, th0, dph), ref, rel_tol=1e-12, abs_tol=1e-15)
+
+
+@pytest.mark.parametrize("r0,th0,th1,dph", [(0.0, 0.2, 0.35, 0.1), (1.0, 1.4, 1.6, 0.125), (2.0, 0.0, 0.1, 0.2)])
+def test_cell_volume_is_pyramid_frustum(orc, r0, th0, th1, dph):
+    r1 = r0 + 0.7
+    # the cell is a frustum of the pyramid with apex at the origin over the
+    # outer r face: V = (A_1 h_1 / 3)(r1^3 - r0^3), A_1 the unit-radius face
+    # area and h_1 its plane's distance from the origin
+    A1 = orc.face_area_r(1.0, th0, th1, dph)
+    thm = 0.5 * (th0 + th1)
+    c = math.cos(dph / 2)
+    h1 = c * math.cos(th0 - thm) / math.hypot(math.sin(thm), c * math.cos(thm))
+    ref = A1 * h1 / 3.0 * (r1 ** 3 - r0 ** 3)
+    assert math.isclose(orc.cell_volume(r0, r1, th0, th1, dph), ref, rel_tol=1e-12)
+
+
+def test_volumes_fill_sphere_wedge(orc):
+    # fine grid: the flat-faced cells converge to the spherical wedge volume
+    n = 64
+    th = np.linspace(0, math.pi, n + 1)
+    dph = 0.02
+    v = sum(orc.cell_volume(0.0, 1.0, th[b], th[b + 1], dph) for b in range(n))
+    assert math.isclose(v, 2.0 / 3.0 * dph, rel_tol=1e-3)
