@@ -1,0 +1,336 @@
+"""Benchmark of the transport step on GB300.
+
+One "step" = the whole hot path on one synthetic background: the time remap
+to a new background (backgrounds B0/B1 alternate every step), the fused face
+fluxes + collision kernel, and the outflow/moment reductions.  The metric is
+zone-group-angle updates per second (species included) of a full step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config3]
+                  [--precision mixed|fp64] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (single thread) on a bounded
+sample of zones of the same workload.  Under torchrun (N > 1) every rank runs
+an independent replica; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "zone·group·angle updates/sec per full step vs plain FP64 GPU path at ≤1e-4 rel L1"
+UNIT = "zone·group·angle·species updates/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def hbm_peak(d):
+    for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs", "copy_gbs"):
+        if k in d:
+            v = d[k]
+            if isinstance(v, dict):
+                v = v.get("value", v.get("burst", None))
+            if v:
+                return float(v)
+    return 6800.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_init(n_gpus):
+    import torch
+    rank, world = 0, 1
+    if n_gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        rank, world = dist.get_rank(), dist.get_world_size()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world
+
+
+def algorithmic_bytes_per_bin(prob, mixed):
+    """Bytes that one full step must move per zone-group-angle-species bin:
+    read f^n and write f^{n+1}, plus the opacities (3 float64 per zone, group
+    and species, amortised over the angles) and the per-zone background (7
+    float64, amortised over groups, angles and species)."""
+    fb = 4 if mixed else 8
+    return 2 * fb + 24.0 / prob.n_ang + 56.0 / (prob.n_ang * prob.n_eps * prob.n_species)
+
+
+def run_ours(args):
+    import torch
+    from paper_2003_02845_gb300 import build, bt, workloads as W
+    rank, world = dist_init(args.gpus)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    build.build()
+    prob = W.by_name(args.workload)
+    mixed = args.precision == "mixed"
+    stream = torch.cuda.Stream()
+    t = bt.Transport(prob, args.precision, stream=stream)
+    B = prob.backgrounds
+    # device-resident copies of both backgrounds
+    dev = []
+    for bg in B:
+        dev.append([torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+                    for x in (bg.v, bg.alpha, bg.phi, bg.kappa_a, bg.kappa_s, bg.f_eq)])
+    torch.cuda.synchronize()
+    t.set_background(B[0])
+    t.set_f(prob.f0)
+    dt = t.max_dt(prob.cfl)
+    bins = prob.n_bins
+    units_per_step = bins
+
+    def one_step(k):
+        d = dev[(k + 1) % 2]
+        t.set_background_device(*d)
+        t.step(dt)
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    l0 = t.launch_count
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.steps):
+            one_step(args.warmup + k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = t.launch_count - l0
+    if world > 1:
+        x = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        ms = float(x.item())
+        torch.distributed.barrier()
+
+    # per-kernel durations with CUDA events on the transport stream
+    t.profile(True)
+    for k in range(args.steps):
+        one_step(args.warmup + args.steps + k)
+    flux_ms, flux_n = t.profile_read(bt.K_FLUX)
+    remap_ms, remap_n = t.profile_read(bt.K_TIME_REMAP)
+    t.profile(False)
+
+    # end to end through the C ABI with host buffers: pinned host background in,
+    # source terms out, every step
+    pinned = []
+    for bg in B:
+        pinned.append([torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).pin_memory()
+                       for x in (bg.rho, bg.T, bg.Ye, bg.v, bg.alpha, bg.phi, bg.shift,
+                                 bg.kappa_a, bg.kappa_s, bg.f_eq)])
+    S, Z = prob.n_species, prob.n_zone
+    outs = [torch.empty(s, dtype=torch.float64).pin_memory() for s in ((S, Z), (S, Z), (S, Z, 3), (Z,))]
+    h2d = sum(x.numel() * 8 for x in pinned[0][3:6] + pinned[0][7:10])
+    d2h = sum(x.numel() * 8 for x in outs)
+    L = bt.lib()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        p = pinned[(k + 1) % 2]
+        bt._check(L.bt_set_background(t.h, bt.BT_MEM_HOST, *[x.data_ptr() for x in p]))
+        t.step(dt)
+        bt._check(L.bt_moments(t.h, bt.BT_MEM_HOST, *[x.data_ptr() for x in outs]))
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        x = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(x.item())
+
+    peaks, peak_src = load_peaks()
+    bpb = algorithmic_bytes_per_bin(prob, mixed)
+    flux_avg_ms = flux_ms / max(flux_n, 1)
+    achieved = bins * bpb / (flux_avg_ms * 1e-3) / 1e9
+    peak = hbm_peak(peaks)
+    res = {
+        "metric": METRIC,
+        "value": world * units_per_step / (ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if mixed else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": prob.name,
+            "precision": args.precision + (" (f32 f/fluxes/remap, f64 collision and sums)" if mixed else ""),
+            "zones": prob.n_zone, "groups": prob.n_eps, "angles": prob.n_ang, "species": prob.n_species,
+            "bins_per_step": bins,
+            "updates_per_s_without_species": world * prob.n_zone * prob.n_eps * prob.n_ang / (ms * 1e-3),
+            "l2": "inputs larger than L2 (f is %.0f MB per buffer)" % (bins * (4 if mixed else 8) / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "backgrounds": "B0/B1 alternate every step (time remap active)",
+        },
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": {"value": world * units_per_step / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {
+            "kernel": "k_flux_collide",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": None,
+            "algorithmic_bytes_per_bin": bpb,
+            "avg_launch_ms": flux_avg_ms,
+            "time_remap_avg_ms": remap_ms / max(remap_n, 1),
+        },
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(prob, budget_s=15.0, steps=1):
+    """The FP64 oracle, single thread, on a bounded sample of zones of the
+    same workload (one subset step after the time remap has been applied)."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(prob)
+    o.set_background(prob.backgrounds[0])
+    o.set_f(prob.f0)
+    dt = o.max_dt(prob.cfl)
+    rng = np.random.default_rng(0)
+    n = 4
+    spent, done_bins = 0.0, 0
+    while spent < budget_s:
+        zones = rng.choice(prob.n_zone, min(n, prob.n_zone), replace=False)
+        t0 = time.perf_counter()
+        o.step_zones(dt, zones)
+        el = time.perf_counter() - t0
+        spent += el
+        done_bins += len(zones) * prob.n_species * prob.n_eps * prob.n_ang
+        n = min(n * 2, prob.n_zone)
+        if n >= prob.n_zone and spent > 0.2 * budget_s:
+            break
+    return {"value": done_bins / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d zone updates (all species, groups, angles) of %s by the single-threaded FP64 "
+                      "oracle in %.1f s, static background (time remap not in the sample)"
+                      % (done_bins // (prob.n_species * prob.n_eps * prob.n_ang), prob.name, spent)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2003_02845_gb300 import workloads as W
+    prob = W.by_name(args.workload)
+    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        cpu_baseline(prob, 1.0)
+    vals = [cpu_baseline(prob, per_step) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    res = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": prob.n_bins / v * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": prob.name, "precision": "fp64 oracle (CPU)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="config3")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

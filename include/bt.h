@@ -1,0 +1,176 @@
+/*
+ * bt.h -- C ABI of the GB300 discrete-ordinate neutrino transport step.
+ *
+ * Implements one time step of the Boltzmann transport scheme of Chan &
+ * Mueller, "A Novel Multi-Dimensional Boltzmann Neutrino Transport Scheme
+ * for Core-Collapse Supernovae" (arXiv:2003.02845): the distribution
+ * f(r, theta, eps, mu, Phi) of each species is advanced by
+ *   (Sec. 3.2, Eq. transformation)  a time remap of every zone from the old
+ *        background's comoving frame to the new one (Lorentz boost, conformal
+ *        frame change, Hamiltonian kick);
+ *   (Sec. 3.3, Eq. fullstep, Eq. halfstep) unsplit interface fluxes on every
+ *        radial, polar and azimuthal face: a locally implicit Lax-Wendroff
+ *        half step blended with an MC-limited upwind state (Sec. 3.3.3), with
+ *        the face and neighbour contents mapped between comoving frames by
+ *        the conservative trilinear remap T (Sec. 3.2);
+ *   (Sec. 3.5) the local implicit absorption/emission/isotropic-scattering
+ *        solve per zone and energy group (Sherman-Morrison form);
+ *   (Sec. 3.4, Eq. hydrosource) the number/energy/momentum source terms.
+ * Every step runs in CUDA kernels built for sm_103a; there is no CPU path.
+ *
+ * Conventions
+ *   Units: c = 1; lengths and dt in the same length unit; kappa per length.
+ *   Zones: zone = b * n_r + a (a radial, b polar).
+ *   Angles: ang = j * n_phi + k (mu index j over Gauss-Legendre nodes in
+ *           ascending order, Phi index k with centres (k + 1/2) 2pi/n_phi).
+ *   f layout: f[s][zone][group][ang], float64 (BT_FP64) or float32 (BT_MIXED).
+ *   Opacity layout: [s][zone][group]; vectors [zone][3] as (r, theta, phi)
+ *           components in the zone's local orthonormal triad.
+ *   Pointers: every array argument is a HOST pointer unless the argument
+ *           `mem` says BT_MEM_DEVICE (then a device pointer on the handle's
+ *           device).  The caller keeps ownership; the library copies.
+ *   Streams: all device work is enqueued on bt_config.stream (a
+ *           cudaStream_t, 0 = legacy default stream).  Calls that return data
+ *           to host memory synchronise that stream.
+ *   Errors: functions return BT_OK (0) or a negative BT_ERR_* code;
+ *           bt_last_error() returns a thread-local message for the last
+ *           failure.  No exception crosses the ABI.
+ *   Threads: one handle must not be used by two host threads at once.
+ */
+#ifndef BT_H_
+#define BT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BT_OK = 0,
+  BT_ERR_ARG = -1,        /* null pointer, bad size or unsupported configuration */
+  BT_ERR_BACKGROUND = -2, /* NaN/Inf, alpha <= 0, phi <= 0, |v| >= 1, kappa < 0, shift != 0 */
+  BT_ERR_DT = -3,         /* dt <= 0 or not finite */
+  BT_ERR_CUDA = -4,       /* a CUDA runtime call failed (message has the CUDA error) */
+  BT_ERR_NUMERIC = -5,    /* non-finite value produced by a step */
+  BT_ERR_STATE = -6       /* call order violated (e.g. step before a background) */
+};
+
+enum { BT_GEOM_SPHERICAL = 0, BT_GEOM_SLAB = 1 };
+enum { BT_FP64 = 0, BT_MIXED = 1 };
+enum { BT_MEM_HOST = 0, BT_MEM_DEVICE = 1 };
+enum { BT_NUE = 0, BT_NUEBAR = 1, BT_NUX = 2 };
+
+typedef struct bt_handle bt_handle;
+
+/*
+ * Problem description (Sec. 3.1, Discretisation).
+ *  geom           BT_GEOM_SPHERICAL: flat-faced cells on spherical-polar vertices
+ *                 (Sec. 3.1); a single periodic azimuthal wedge of width
+ *                 dphi_wedge (Sec. 3.3.4).  If theta_periodic == 1 the grid is a
+ *                 1D column (n_theta must be 1) centred on the equator with
+ *                 periodic polar faces of width dtheta_column; otherwise the
+ *                 polar range is [0, pi] split uniformly into n_theta >= 2 rows.
+ *                 BT_GEOM_SLAB: plane-parallel z grid (r_edges are z edges),
+ *                 unit face areas, open boundaries at both ends.
+ *  r_edges        n_r + 1 increasing radii (host pointer, copied).  r_edges[0]
+ *                 == 0 gives a zero-area inner face; r_edges[0] > 0 a
+ *                 reflecting wall (spherical geometry).
+ *  species_kind   n_species entries of BT_NUE/BT_NUEBAR/BT_NUX (host, copied).
+ *  eps_edges      n_eps + 1 log-uniform group edges (constant ratio; host).
+ *  n_mu, n_phi    angular grid: Gauss-Legendre mu cells x uniform Phi cells.
+ *  precision      BT_FP64 or BT_MIXED (float32 f, fluxes and remap; float64
+ *                 collision solve, content accumulators and sums).
+ *  phase_norm     the 1/h^3 factor of the hydro source terms (Eq. hydrosource).
+ *  stream         cudaStream_t for all work of this handle.
+ */
+typedef struct bt_config {
+  int32_t geom;
+  int32_t n_r, n_theta;
+  const double* r_edges;
+  int32_t theta_periodic;
+  double dtheta_column;
+  double dphi_wedge;
+  int32_t n_species;
+  const int32_t* species_kind;
+  int32_t n_eps;
+  const double* eps_edges;
+  int32_t n_mu, n_phi;
+  int32_t precision;
+  double phase_norm;
+  void* stream;
+} bt_config;
+
+/* Message of the last failed call on this host thread (never NULL). */
+const char* bt_last_error(void);
+
+/* Device bytes bt_create will use for this configuration (0 on error). */
+size_t bt_workspace_bytes(const bt_config* cfg);
+
+/* Validate cfg, build the geometry and momentum tables (Sec. 3.1) in float64
+ * on the host, and upload them.  workspace: NULL (the library allocates with
+ * cudaMalloc) or a device pointer to at least bt_workspace_bytes(cfg) bytes,
+ * 256-byte aligned, that the caller keeps alive until bt_destroy.  f starts
+ * at zero.  *out receives the handle. */
+int bt_create(const bt_config* cfg, void* workspace, bt_handle** out);
+int bt_destroy(bt_handle* h);
+
+/* Fluid and metric background and opacities (Sec. 3.1 CFC metric, Sec. 3.2.2,
+ * Sec. 3.2.3, Sec. 3.4): per zone v[3], lapse alpha, conformal factor phi,
+ * shift[3] (must be zero); per (s, zone, group) kappa_a, kappa_s, f_eq.
+ * rho, T, Ye are accepted for the caller's bookkeeping and not used (the
+ * opacities are given).  Any may be NULL except v, alpha, phi, kappa_a,
+ * kappa_s, f_eq.  A background set after an earlier one makes the next
+ * bt_step first remap f from the earlier background's comoving frames to the
+ * new ones (Sec. 3.2, time remap). */
+int bt_set_background(bt_handle* h, int mem,
+                      const double* rho, const double* T, const double* Ye,
+                      const double* v, const double* alpha, const double* phi,
+                      const double* shift,
+                      const double* kappa_a, const double* kappa_s, const double* f_eq);
+
+/* Copy f in/out (layout above; float64 for BT_FP64, float32 for BT_MIXED).
+ * bt_set_f takes f as given in the current background's comoving frames and
+ * cancels a pending time remap. */
+int bt_set_f(bt_handle* h, int mem, const void* f);
+int bt_get_f(bt_handle* h, int mem, void* f);
+
+/* Courant limit (Sec. 3.3, global timestep limited by the smallest cell): the
+ * largest dt for which no bin of any zone loses more than `cfl` of its
+ * content through its faces in one step. */
+int bt_max_dt(bt_handle* h, double cfl, double* dt_out);
+
+/* One transport step of length dt (Sec. 3.3 Eq. fullstep, Sec. 3.5). */
+int bt_step(bt_handle* h, double dt);
+
+/* Collision source terms of the last step (Eq. hydrosource), per unit
+ * coordinate volume and time: dN[s][zone], dE[s][zone] (comoving energy),
+ * dP[s][zone][3] (comoving momentum, local triad), Q_Ye[zone] =
+ * -(dN_nue - dN_nuebar) * phase_norm.  Any output may be NULL. */
+int bt_moments(bt_handle* h, int mem, double* dN, double* dE, double* dP, double* Q_Ye);
+
+/* Per-species totals (host arrays of n_species): number N = sum dV phi^6 u^0
+ * dGamma dOmega f; energy at infinity E (lab energy eps u^0 times alpha);
+ * cumulative number and energy that left through open boundaries. */
+int bt_totals(bt_handle* h, double* N, double* E, double* N_out, double* E_out);
+
+/* Comoving angular moments J, H, K per [s][zone][group] (Sec. 4.1). */
+int bt_jhk(bt_handle* h, int mem, double* J, double* H, double* K);
+
+/* Number of device kernel launches this handle has issued (for accounting). */
+int64_t bt_launch_count(const bt_handle* h);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every launch of bt_step while enabled (enable = 1), for measurement.
+ * bt_profile(h, 1) also clears the records.  bt_profile_read synchronises
+ * the stream and returns, for kernel id BT_K_TIME_REMAP / BT_K_FLUX /
+ * BT_K_OUTFLOW, the summed duration in ms and the number of launches. */
+enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2 };
+int bt_profile(bt_handle* h, int enable);
+int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BT_H_ */

@@ -1,0 +1,237 @@
+"""Python binding of the C ABI in include/bt.h (argument marshalling only).
+
+Every step of the transport update runs in the CUDA kernels of
+``_build/libbt.so``; this module only converts arguments.  PyTorch provides
+the device workspace and the stream.  If the library is missing the import
+of ``lib()`` raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BT_OK = 0
+BT_GEOM_SPHERICAL, BT_GEOM_SLAB = 0, 1
+BT_FP64, BT_MIXED = 0, 1
+BT_MEM_HOST, BT_MEM_DEVICE = 0, 1
+
+_lib = None
+
+
+class BtConfig(C.Structure):
+    _fields_ = [
+        ("geom", C.c_int32), ("n_r", C.c_int32), ("n_theta", C.c_int32),
+        ("r_edges", C.POINTER(C.c_double)),
+        ("theta_periodic", C.c_int32), ("dtheta_column", C.c_double), ("dphi_wedge", C.c_double),
+        ("n_species", C.c_int32), ("species_kind", C.POINTER(C.c_int32)),
+        ("n_eps", C.c_int32), ("eps_edges", C.POINTER(C.c_double)),
+        ("n_mu", C.c_int32), ("n_phi", C.c_int32), ("precision", C.c_int32),
+        ("phase_norm", C.c_double), ("stream", C.c_void_p),
+    ]
+
+
+class BtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bt error %d: %s" % (code, msg))
+        self.code = code
+
+
+def lib():
+    """Load libbt.so (built in-tree by ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA transport library not built: %s (run __graft_entry__.build())" % path)
+        L = C.CDLL(path)
+        vp, dp, i32 = C.c_void_p, C.c_void_p, C.c_int
+        L.bt_last_error.restype = C.c_char_p
+        L.bt_workspace_bytes.restype = C.c_size_t
+        L.bt_workspace_bytes.argtypes = [C.POINTER(BtConfig)]
+        L.bt_create.argtypes = [C.POINTER(BtConfig), vp, C.POINTER(vp)]
+        L.bt_destroy.argtypes = [vp]
+        L.bt_set_background.argtypes = [vp, i32] + [dp] * 10
+        L.bt_set_f.argtypes = [vp, i32, vp]
+        L.bt_get_f.argtypes = [vp, i32, vp]
+        L.bt_max_dt.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
+        L.bt_step.argtypes = [vp, C.c_double]
+        L.bt_moments.argtypes = [vp, i32, dp, dp, dp, dp]
+        L.bt_totals.argtypes = [vp, dp, dp, dp, dp]
+        L.bt_jhk.argtypes = [vp, i32, dp, dp, dp]
+        L.bt_launch_count.restype = C.c_int64
+        L.bt_launch_count.argtypes = [vp]
+        L.bt_profile.argtypes = [vp, i32]
+        L.bt_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != BT_OK:
+        raise BtError(rc, lib().bt_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()          # torch tensor
+
+
+def _host64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Transport:
+    """One transport problem on the current CUDA device.
+
+    prob: a ``workloads.Problem`` (geometry, grids, species).
+    precision: "fp64" or "mixed".
+    """
+
+    def __init__(self, prob, precision: str = "fp64", stream=None, phase_norm: float = 1.0):
+        import torch
+        L = lib()
+        self.prob = prob
+        self.mixed = precision == "mixed"
+        self.fdtype = np.float32 if self.mixed else np.float64
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._r = _host64(prob.r_edges)
+        self._e = _host64(prob.eps_edges)
+        self._k = np.ascontiguousarray(np.asarray(prob.species_kind, dtype=np.int32))
+        cfg = BtConfig()
+        cfg.geom = prob.geom
+        cfg.n_r = prob.n_r
+        cfg.n_theta = prob.n_theta
+        cfg.r_edges = self._r.ctypes.data_as(C.POINTER(C.c_double))
+        cfg.theta_periodic = int(prob.theta_periodic)
+        cfg.dtheta_column = float(prob.dtheta_column)
+        cfg.dphi_wedge = float(prob.dphi)
+        cfg.n_species = prob.n_species
+        cfg.species_kind = self._k.ctypes.data_as(C.POINTER(C.c_int32))
+        cfg.n_eps = prob.n_eps
+        cfg.eps_edges = self._e.ctypes.data_as(C.POINTER(C.c_double))
+        cfg.n_mu = prob.n_mu
+        cfg.n_phi = prob.n_phi
+        cfg.precision = BT_MIXED if self.mixed else BT_FP64
+        cfg.phase_norm = phase_norm
+        cfg.stream = self.stream.cuda_stream
+        self.cfg = cfg
+        nbytes = L.bt_workspace_bytes(C.byref(cfg))
+        if nbytes == 0:
+            raise BtError(-1, L.bt_last_error().decode())
+        # workspace from PyTorch's allocator, kept alive by this object
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        h = C.c_void_p()
+        _check(L.bt_create(C.byref(cfg), C.c_void_p(aligned), C.byref(h)))
+        self.h = h
+        self.shape = (prob.n_species, prob.n_zone, prob.n_eps, prob.n_ang)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- inputs -------------------------------------------------------------
+    def set_background(self, bg):
+        """Host (numpy) background: copied host -> device on the stream."""
+        arrs = [_host64(bg.rho), _host64(bg.T), _host64(bg.Ye), _host64(bg.v), _host64(bg.alpha),
+                _host64(bg.phi), _host64(bg.shift), _host64(bg.kappa_a), _host64(bg.kappa_s), _host64(bg.f_eq)]
+        _check(lib().bt_set_background(self.h, BT_MEM_HOST, *[_ptr(a) for a in arrs]))
+        self._keep_bg = arrs
+
+    def set_background_device(self, v, alpha, phi, kappa_a, kappa_s, f_eq):
+        """Device (torch float64, contiguous) background."""
+        _check(lib().bt_set_background(self.h, BT_MEM_DEVICE, None, None, None, _ptr(v), _ptr(alpha), _ptr(phi),
+                                       None, _ptr(kappa_a), _ptr(kappa_s), _ptr(f_eq)))
+
+    def set_f(self, f):
+        if isinstance(f, np.ndarray):
+            a = np.ascontiguousarray(f.astype(self.fdtype, copy=False).reshape(self.shape))
+            _check(lib().bt_set_f(self.h, BT_MEM_HOST, _ptr(a)))
+            self.torch.cuda.synchronize()
+        else:
+            _check(lib().bt_set_f(self.h, BT_MEM_DEVICE, _ptr(f)))
+
+    # -- step ---------------------------------------------------------------
+    def max_dt(self, cfl: float) -> float:
+        out = C.c_double()
+        _check(lib().bt_max_dt(self.h, float(cfl), C.byref(out)))
+        return out.value
+
+    def step(self, dt: float):
+        _check(lib().bt_step(self.h, float(dt)))
+
+    # -- outputs ------------------------------------------------------------
+    def get_f(self, out=None) -> np.ndarray:
+        if out is not None:
+            _check(lib().bt_get_f(self.h, BT_MEM_DEVICE if not isinstance(out, np.ndarray) else BT_MEM_HOST, _ptr(out)))
+            return out
+        a = np.empty(self.shape, dtype=self.fdtype)
+        _check(lib().bt_get_f(self.h, BT_MEM_HOST, _ptr(a)))
+        return a
+
+    def moments(self, out=None):
+        S, Z = self.prob.n_species, self.prob.n_zone
+        if out is None:
+            out = (np.empty((S, Z)), np.empty((S, Z)), np.empty((S, Z, 3)), np.empty(Z))
+        mem = BT_MEM_HOST if isinstance(out[0], np.ndarray) else BT_MEM_DEVICE
+        _check(lib().bt_moments(self.h, mem, *[_ptr(a) for a in out]))
+        return out
+
+    def totals(self):
+        S = self.prob.n_species
+        N, E, No, Eo = np.empty(S), np.empty(S), np.empty(S), np.empty(S)
+        _check(lib().bt_totals(self.h, _ptr(N), _ptr(E), _ptr(No), _ptr(Eo)))
+        return N, E, No, Eo
+
+    def jhk(self):
+        sh = (self.prob.n_species, self.prob.n_zone, self.prob.n_eps)
+        J, H, K = np.empty(sh), np.empty(sh), np.empty(sh)
+        _check(lib().bt_jhk(self.h, BT_MEM_HOST, _ptr(J), _ptr(H), _ptr(K)))
+        return J, H, K
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().bt_launch_count(self.h))
+
+    def profile(self, enable: bool):
+        _check(lib().bt_profile(self.h, int(enable)))
+
+    def profile_read(self, kernel: int):
+        ms, n = C.c_double(), C.c_int64()
+        _check(lib().bt_profile_read(self.h, int(kernel), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+
+K_TIME_REMAP, K_FLUX, K_OUTFLOW = 0, 1, 2
+
+
+def run(prob, precision="fp64", n_steps=None, dt=None, cfl=None):
+    """Same protocol as the oracle's ``run``: background 0 (alternating with
+    background 1 every step if prob.alternate), f0, n_steps steps."""
+    t = Transport(prob, precision)
+    t.set_background(prob.backgrounds[0])
+    t.set_f(prob.f0)
+    if dt is None:
+        dt = t.max_dt(prob.cfl if cfl is None else cfl)
+    n = prob.n_steps if n_steps is None else n_steps
+    for k in range(n):
+        if prob.alternate and len(prob.backgrounds) > 1:
+            t.set_background(prob.backgrounds[(k + 1) % 2])
+        t.step(dt)
+    return t, dt

@@ -1,0 +1,662 @@
+// bt_host.cpp -- host side of the transport library: configuration checks,
+// float64 geometry and momentum tables (Sec. 3.1), device workspace, and the
+// C ABI declared in include/bt.h.  All arithmetic of the step runs in the
+// kernels of bt_kernels.cu; this file only prepares tables and launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bt.h"
+#include "bt_internal.h"
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(BT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Gauss-Legendre nodes/weights: Newton iteration on P_n from Tricomi's
+// asymptotic initial guess; nodes mirrored to be exactly antisymmetric.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 1; i <= (n + 1) / 2; ++i) {
+    double t = kPi * (4.0 * i - 1.0) / (4.0 * n + 2.0);
+    double z = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(t);
+    double dp = 0.0;
+    for (int it = 0; it < 60; ++it) {
+      double pm = 1.0, pc = z;
+      for (int k = 2; k <= n; ++k) {
+        double pn = ((2.0 * k - 1.0) * z * pc - (k - 1.0) * pm) / k;
+        pm = pc;
+        pc = pn;
+      }
+      if (n == 1) { pc = z; pm = 1.0; }
+      dp = n * (pm - z * pc) / (1.0 - z * z);
+      double dz = pc / dp;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-17) break;
+    }
+    {
+      double pm = 1.0, pc = z;
+      for (int k = 2; k <= n; ++k) {
+        double pn = ((2.0 * k - 1.0) * z * pc - (k - 1.0) * pm) / k;
+        pm = pc;
+        pc = pn;
+      }
+      if (n == 1) { pc = z; pm = 1.0; }
+      dp = n * (pm - z * pc) / (1.0 - z * z);
+    }
+    double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[n - i] = z;
+    x[i - 1] = -z;
+    w[n - i] = wi;
+    w[i - 1] = wi;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// local triad (r_hat, theta_hat, phi_hat) as columns, row-major E[3*m + c]
+void triad(double th, double ph, double E[9]) {
+  double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
+  double c0[3] = {st * cp, st * sp, ct}, c1[3] = {ct * cp, ct * sp, -st}, c2[3] = {-sp, cp, 0.0};
+  for (int m = 0; m < 3; ++m) { E[3 * m] = c0[m]; E[3 * m + 1] = c1[m]; E[3 * m + 2] = c2[m]; }
+}
+
+// components in the src triad -> components in the dst triad: G = E_dst^T E_src
+void rotation(double ths, double phs, double thd, double phd, double* G) {
+  double Es[9], Ed[9];
+  triad(ths, phs, Es);
+  triad(thd, phd, Ed);
+  for (int m = 0; m < 3; ++m)
+    for (int n = 0; n < 3; ++n) G[3 * m + n] = Ed[m] * Es[n] + Ed[3 + m] * Es[3 + n] + Ed[6 + m] * Es[6 + n];
+}
+
+// Closed forms of the flat-faced cell geometry (Sec. 3.1).
+// radial face at radius r: isosceles trapezoid of the chords 2 r sin(th) sin(dph/2)
+double area_r(double r, double th0, double th1, double dph) {
+  double c = std::cos(0.5 * dph), s = std::sin(0.5 * dph);
+  double h = r * std::hypot(c * (std::sin(th1) - std::sin(th0)), std::cos(th1) - std::cos(th0));
+  return 0.5 * (2.0 * r * std::sin(th0) * s + 2.0 * r * std::sin(th1) * s) * h;
+}
+// polar face on the cone th: trapezoid between the chords at r0 and r1
+double area_t(double r0, double r1, double th, double dph) {
+  double c = std::cos(0.5 * dph), s = std::sin(0.5 * dph);
+  double h = (r1 - r0) * std::hypot(std::sin(th) * c, std::cos(th));
+  return 0.5 * (2.0 * r0 * std::sin(th) * s + 2.0 * r1 * std::sin(th) * s) * h;
+}
+// azimuthal face: difference of two triangles from the origin
+double area_p(double r0, double r1, double th0, double th1) {
+  return 0.5 * std::sin(th1 - th0) * (r1 * r1 - r0 * r0);
+}
+// cell: frustum of the pyramid with apex at the origin over the radial face
+double volume(double r0, double r1, double th0, double th1, double dph) {
+  double thm = 0.5 * (th0 + th1), c = std::cos(0.5 * dph);
+  double h1 = c * std::cos(th0 - thm) / std::hypot(std::sin(thm), c * std::cos(thm));
+  return area_r(1.0, th0, th1, dph) * h1 / 3.0 * (r1 * r1 * r1 - r0 * r0 * r0);
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+struct Layout {
+  size_t total = 0;
+  size_t take(size_t bytes) {
+    size_t o = total;
+    total += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+}  // namespace
+
+struct bt_handle {
+  bt_config cfg;
+  int mixed;
+  bt::Tables tb;
+  bt::State st;
+  cudaStream_t stream;
+  void* ws;
+  bool own_ws;
+  size_t ws_bytes;
+  std::vector<int32_t> kinds;
+  // device buffers
+  double* bg[2][3];   // two background slots: v, alpha, cf
+  int cur;            // index of the current background slot
+  double *ka, *kaf, *ks, *fe;
+  void* f[2];
+  int fcur;
+  double* qye;
+  double* tmp;        // small device scratch (rates, totals)
+  bool has_bg, remap_pending;
+  int64_t launches;
+  size_t nzone, nbin_total, fbytes;
+  // profiling: (kernel id, start, stop) per launch while enabled
+  bool prof;
+  std::vector<int> prof_id;
+  std::vector<cudaEvent_t> prof_ev;
+};
+
+namespace {
+
+// Offsets of every device buffer inside one workspace.
+struct WsPlan {
+  size_t tables[32];
+  size_t bg[2][3], ka, ks, fe, f[2], mom_N, mom_E, mom_P, out_N, out_E, acc, red, flag, qye, tmp;
+  size_t total;
+};
+
+int plan(const bt_config* c, WsPlan& P, size_t* tab_sizes) {
+  const size_t nz = (size_t)c->n_r * c->n_theta;
+  const size_t ns = c->n_species, ne = c->n_eps, nang = (size_t)c->n_mu * c->n_phi;
+  const size_t nth = c->n_theta;
+  const size_t fel = c->precision == BT_MIXED ? 4 : 8;
+  Layout L;
+  size_t sizes[] = {
+      (size_t)c->n_mu, (size_t)c->n_mu, (size_t)c->n_phi, (size_t)c->n_phi, nang, ne, ne, nz,
+      (size_t)c->n_r + 1, (size_t)c->n_r, nth + 1, nth,
+      nth * (c->n_r + 1), (nth + 1) * c->n_r, nth * c->n_r,
+      nth * 9, (nth + 1) * 4 * 9, nth * 4 * 9};
+  const int ntab = sizeof(sizes) / sizeof(sizes[0]);
+  for (int i = 0; i < ntab; ++i) {
+    tab_sizes[i] = sizes[i];
+    P.tables[i] = L.take(8 * sizes[i]);
+  }
+  P.tables[ntab] = L.take(4 * ns);  // species kinds
+  for (int s = 0; s < 2; ++s) {
+    P.bg[s][0] = L.take(8 * 3 * nz);
+    P.bg[s][1] = L.take(8 * nz);
+    P.bg[s][2] = L.take(8 * nz);
+  }
+  P.ka = L.take(8 * ns * nz * ne);
+  P.ks = L.take(8 * ns * nz * ne);
+  P.fe = L.take(8 * ns * nz * ne);
+  P.f[0] = L.take(fel * ns * nz * ne * nang);
+  P.f[1] = L.take(fel * ns * nz * ne * nang);
+  P.mom_N = L.take(8 * ns * nz);
+  P.mom_E = L.take(8 * ns * nz);
+  P.mom_P = L.take(8 * 3 * ns * nz);
+  P.out_N = L.take(8 * ns * nz);
+  P.out_E = L.take(8 * ns * nz);
+  P.acc = L.take(8 * 4 * ns);
+  P.red = L.take(8 * 2 * ns * nz);
+  P.flag = L.take(16);
+  P.qye = L.take(8 * nz);
+  P.tmp = L.take(8 * (4 * ns + 8));
+  P.total = L.total;
+  return ntab;
+}
+
+int validate(const bt_config* c) {
+  if (!c) return fail(BT_ERR_ARG, "cfg is NULL");
+  if (c->geom != BT_GEOM_SPHERICAL && c->geom != BT_GEOM_SLAB) return fail(BT_ERR_ARG, "unknown geom");
+  if (c->n_r < 1 || c->n_theta < 1) return fail(BT_ERR_ARG, "n_r and n_theta must be >= 1");
+  if (!c->r_edges || !c->eps_edges) return fail(BT_ERR_ARG, "r_edges/eps_edges NULL");
+  for (int a = 0; a < c->n_r; ++a)
+    if (!(c->r_edges[a + 1] > c->r_edges[a])) return fail(BT_ERR_ARG, "r_edges must increase");
+  if (c->geom == BT_GEOM_SPHERICAL && c->r_edges[0] < 0.0) return fail(BT_ERR_ARG, "r_edges[0] < 0");
+  if (c->geom == BT_GEOM_SLAB && c->n_theta != 1) return fail(BT_ERR_ARG, "slab needs n_theta == 1");
+  if (c->geom == BT_GEOM_SPHERICAL) {
+    if (c->theta_periodic) {
+      if (c->n_theta != 1) return fail(BT_ERR_ARG, "a column needs n_theta == 1");
+      if (!(c->dtheta_column > 0.0 && c->dtheta_column < 1.0)) return fail(BT_ERR_ARG, "dtheta_column out of (0, 1)");
+    } else if (c->n_theta < 2) {
+      return fail(BT_ERR_ARG, "2D grids need n_theta >= 2");
+    }
+    if (!(c->dphi_wedge > 0.0 && c->dphi_wedge < 1.0)) return fail(BT_ERR_ARG, "dphi_wedge out of (0, 1)");
+  }
+  if (c->n_species < 1 || !c->species_kind) return fail(BT_ERR_ARG, "species");
+  if (c->n_eps < 1 || c->n_eps > bt::kMaxEps) return fail(BT_ERR_ARG, "n_eps out of range");
+  if (c->n_mu < 1 || c->n_mu > bt::kMaxMu || c->n_phi < 1 || c->n_mu * c->n_phi > bt::kMaxAng)
+    return fail(BT_ERR_ARG, "angular grid out of range");
+  for (int i = 0; i <= c->n_eps; ++i)
+    if (!(c->eps_edges[i] > 0.0) || (i > 0 && !(c->eps_edges[i] > c->eps_edges[i - 1])))
+      return fail(BT_ERR_ARG, "eps_edges must be positive and increasing");
+  if (c->n_eps >= 2) {
+    double q0 = c->eps_edges[1] / c->eps_edges[0];
+    for (int i = 1; i < c->n_eps; ++i) {
+      double q = c->eps_edges[i + 1] / c->eps_edges[i];
+      if (std::fabs(q / q0 - 1.0) > 1e-9) return fail(BT_ERR_ARG, "eps_edges must be log-uniform");
+    }
+  }
+  if (c->precision != BT_FP64 && c->precision != BT_MIXED) return fail(BT_ERR_ARG, "precision");
+  return BT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bt_last_error(void) { return g_err.c_str(); }
+
+size_t bt_workspace_bytes(const bt_config* cfg) {
+  if (validate(cfg) != BT_OK) return 0;
+  WsPlan P;
+  size_t ts[32];
+  plan(cfg, P, ts);
+  return P.total;
+}
+
+int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
+  if (!out) return fail(BT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate(c);
+  if (rc != BT_OK) return rc;
+  bt_handle* h = new bt_handle();
+  h->cfg = *c;
+  h->mixed = c->precision == BT_MIXED;
+  h->stream = (cudaStream_t)c->stream;
+  h->kinds.assign(c->species_kind, c->species_kind + c->n_species);
+  h->cfg.species_kind = h->kinds.data();
+  h->cfg.r_edges = nullptr;
+  h->cfg.eps_edges = nullptr;
+  WsPlan P;
+  size_t ts[32];
+  const int ntab = plan(c, P, ts);
+  h->ws_bytes = P.total;
+  if (workspace) {
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) { delete h; return fail(BT_ERR_ARG, "workspace must be 256-byte aligned"); }
+    h->ws = workspace;
+    h->own_ws = false;
+  } else {
+    cudaError_t e = cudaMalloc(&h->ws, P.total);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaMalloc(workspace)"); }
+    h->own_ws = true;
+  }
+  char* base = static_cast<char*>(h->ws);
+  auto D = [&](size_t off) { return reinterpret_cast<double*>(base + off); };
+
+  // ---- host tables (float64)
+  const int nr = c->n_r, nth = c->n_theta, ne = c->n_eps, nmu = c->n_mu, nph = c->n_phi;
+  const int nang = nmu * nph;
+  const size_t nz = (size_t)nr * nth;
+  const bool slab = c->geom == BT_GEOM_SLAB;
+  const double dph = slab ? 0.0 : c->dphi_wedge;
+  std::vector<double> mu, wmu;
+  gauss_legendre(nmu, mu, wmu);
+  std::vector<double> smu(nmu), cph(nph), sph(nph), dOm(nang), dGam(ne), eps(ne);
+  for (int j = 0; j < nmu; ++j) smu[j] = std::sqrt(1.0 - mu[j] * mu[j]);
+  for (int k = 0; k < nph; ++k) {
+    double P_k = (k + 0.5) * 2.0 * kPi / nph;
+    cph[k] = std::cos(P_k);
+    sph[k] = std::sin(P_k);
+  }
+  for (int j = 0; j < nmu; ++j)
+    for (int k = 0; k < nph; ++k) dOm[j * nph + k] = wmu[j] * 2.0 * kPi / nph;
+  for (int i = 0; i < ne; ++i) {
+    double a = c->eps_edges[i], b = c->eps_edges[i + 1];
+    double a3 = a * a * a, b3 = b * b * b;
+    dGam[i] = (b3 - a3) / 3.0;
+    eps[i] = 0.75 * (b3 * b - a3 * a) / (b3 - a3);   // number-weighted mean energy of the bin
+  }
+  const double R = ne >= 2 ? eps[1] / eps[0] : 2.0;
+  std::vector<double> r_e(c->r_edges, c->r_edges + nr + 1), r_c(nr), th_e(nth + 1), th_c(nth);
+  for (int a = 0; a < nr; ++a) r_c[a] = 0.5 * (r_e[a] + r_e[a + 1]);
+  if (slab) {
+    th_e[0] = 0.0; th_e[1] = 0.0;
+  } else if (c->theta_periodic) {
+    th_e[0] = 0.5 * kPi - 0.5 * c->dtheta_column;
+    th_e[1] = 0.5 * kPi + 0.5 * c->dtheta_column;
+  } else {
+    for (int b = 0; b <= nth; ++b) th_e[b] = kPi * b / nth;
+  }
+  for (int b = 0; b < nth; ++b) th_c[b] = 0.5 * (th_e[b] + th_e[b + 1]);
+  std::vector<double> vol(nz), ar(nth * (nr + 1)), at((nth + 1) * nr, 0.0), ap(nth * nr, 0.0);
+  std::vector<double> Gr(9 * nth, 0.0), Gt(9 * 4 * (nth + 1), 0.0), Gp(9 * 4 * nth, 0.0);
+  for (int b = 0; b < nth; ++b)
+    for (int a = 0; a < nr; ++a)
+      vol[b * nr + a] = slab ? (r_e[a + 1] - r_e[a]) : volume(r_e[a], r_e[a + 1], th_e[b], th_e[b + 1], dph);
+  for (int b = 0; b < nth; ++b)
+    for (int a = 0; a <= nr; ++a)
+      ar[b * (nr + 1) + a] = slab ? 1.0 : area_r(r_e[a], th_e[b], th_e[b + 1], dph);
+  if (!slab) {
+    const double cph2 = std::cos(0.5 * dph);
+    for (int b = 0; b < nth; ++b) {
+      for (int a = 0; a < nr; ++a) ap[b * nr + a] = area_p(r_e[a], r_e[a + 1], th_e[b], th_e[b + 1]);
+      // radial-face triad: colatitude of the flat face's normal
+      double thr = std::atan2(std::sin(th_c[b]), std::cos(th_c[b]) * cph2);
+      rotation(th_c[b], 0.0, thr, 0.0, &Gr[9 * b]);
+      // periodic azimuthal face of row b: images at phi = (k-1) dphi, face at dphi/2
+      for (int k = 0; k < 4; ++k) rotation(th_c[b], (k - 1) * dph, th_c[b], 0.5 * dph, &Gp[9 * (4 * b + k)]);
+    }
+    if (c->theta_periodic) {
+      const double d = c->dtheta_column, thc = th_c[0], the = thc + 0.5 * d;
+      for (int a = 0; a < nr; ++a) at[a] = area_t(r_e[a], r_e[a + 1], the, dph);
+      double tht = std::atan2(std::sin(the) * cph2, std::cos(the));
+      for (int k = 0; k < 4; ++k) rotation(thc + (k - 1) * d, 0.0, tht, 0.0, &Gt[9 * k]);
+    } else {
+      for (int e = 1; e < nth; ++e) {
+        for (int a = 0; a < nr; ++a) at[e * nr + a] = area_t(r_e[a], r_e[a + 1], th_e[e], dph);
+        double tht = std::atan2(std::sin(th_e[e]) * cph2, std::cos(th_e[e]));
+        for (int k = 0; k < 4; ++k) {
+          int bb = e - 2 + k;
+          if (bb >= 0 && bb < nth) rotation(th_c[bb], 0.0, tht, 0.0, &Gt[9 * (4 * e + k)]);
+        }
+      }
+    }
+  }
+  const std::vector<double>* tabs[] = {&mu, &smu, &cph, &sph, &dOm, &dGam, &eps, &vol, &r_e, &r_c,
+                                       &th_e, &th_c, &ar, &at, &ap, &Gr, &Gt, &Gp};
+  for (int i = 0; i < ntab; ++i) {
+    cudaError_t e = cudaMemcpyAsync(base + P.tables[i], tabs[i]->data(), 8 * ts[i], cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { bt_destroy(h); return cuda_fail(e, "upload tables"); }
+  }
+  cudaMemcpyAsync(base + P.tables[ntab], h->kinds.data(), 4 * c->n_species, cudaMemcpyHostToDevice, h->stream);
+
+  bt::Tables& T = h->tb;
+  T.geom = c->geom; T.slab = slab; T.periodic_th = !slab && c->theta_periodic;
+  T.inner_zero = !slab && r_e[0] == 0.0; T.inner_reflect = !slab && r_e[0] > 0.0;
+  T.n_r = nr; T.n_th = nth; T.n_zone = (int)nz; T.n_s = c->n_species; T.n_e = ne;
+  T.n_mu = nmu; T.n_ph = nph; T.n_ang = nang;
+  T.R = R; T.logR = std::log(R); T.dphi = dph; T.dth_col = T.periodic_th ? c->dtheta_column : 0.0;
+  T.mu = D(P.tables[0]); T.smu = D(P.tables[1]); T.cph = D(P.tables[2]); T.sph = D(P.tables[3]);
+  T.dOm = D(P.tables[4]); T.dGam = D(P.tables[5]); T.eps = D(P.tables[6]); T.vol = D(P.tables[7]);
+  T.r_e = D(P.tables[8]); T.r_c = D(P.tables[9]); T.th_e = D(P.tables[10]); T.th_c = D(P.tables[11]);
+  T.area_r = D(P.tables[12]); T.area_t = D(P.tables[13]); T.area_p = D(P.tables[14]);
+  T.G_r = D(P.tables[15]); T.G_t = D(P.tables[16]); T.G_p = D(P.tables[17]);
+  T.species_kind = reinterpret_cast<const int*>(base + P.tables[ntab]);
+
+  for (int s = 0; s < 2; ++s)
+    for (int q = 0; q < 3; ++q) h->bg[s][q] = D(P.bg[s][q]);
+  h->cur = 0;
+  h->ka = D(P.ka); h->ks = D(P.ks); h->fe = D(P.fe);
+  h->f[0] = base + P.f[0]; h->f[1] = base + P.f[1]; h->fcur = 0;
+  h->qye = D(P.qye); h->tmp = D(P.tmp);
+  bt::State& S = h->st;
+  S.mom_N = D(P.mom_N); S.mom_E = D(P.mom_E); S.mom_P = D(P.mom_P);
+  S.out_N = D(P.out_N); S.out_E = D(P.out_E); S.acc = D(P.acc); S.red = D(P.red);
+  S.flag = reinterpret_cast<int*>(base + P.flag);
+  S.ka = h->ka; S.ks = h->ks; S.fe = h->fe;
+  S.qye = h->qye;
+  S.phase_norm = c->phase_norm;
+  h->nzone = nz;
+  h->nbin_total = (size_t)c->n_species * nz * ne * nang;
+  h->fbytes = h->nbin_total * (h->mixed ? 4 : 8);
+  cudaMemsetAsync(h->f[0], 0, h->fbytes, h->stream);
+  cudaMemsetAsync(S.acc, 0, 8 * 4 * c->n_species, h->stream);
+  cudaMemsetAsync(S.flag, 0, 16, h->stream);
+  cudaMemsetAsync(S.mom_N, 0, 8 * c->n_species * nz, h->stream);
+  cudaMemsetAsync(S.mom_E, 0, 8 * c->n_species * nz, h->stream);
+  cudaMemsetAsync(S.mom_P, 0, 8 * 3 * c->n_species * nz, h->stream);
+  cudaMemsetAsync(h->qye, 0, 8 * nz, h->stream);
+  h->launches = 0;
+  h->prof = false;
+  h->has_bg = false;
+  h->remap_pending = false;
+  // shared memory per CTA must fit the opt-in limit
+  size_t need = std::max(bt::flux_smem_bytes(T, h->mixed), bt::remap_smem_bytes(T, h->mixed));
+  int lim = bt::max_optin_smem();
+  if ((long)need > (long)lim) {
+    bt_destroy(h);
+    return fail(BT_ERR_ARG, "problem needs " + std::to_string(need) + " bytes of shared memory per CTA (limit " +
+                                std::to_string(lim) + ")");
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) { bt_destroy(h); return cuda_fail(e, "bt_create"); }
+  *out = h;
+  return BT_OK;
+}
+
+static void prof_clear(bt_handle* h) {
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  h->prof_ev.clear();
+  h->prof_id.clear();
+}
+
+// record an event pair around one launch while profiling is on
+struct ProfScope {
+  bt_handle* h;
+  int id;
+  cudaEvent_t a = nullptr;
+  ProfScope(bt_handle* hh, int kid) : h(hh), id(kid) {
+    if (!h->prof) return;
+    cudaEventCreate(&a);
+    cudaEventRecord(a, h->stream);
+  }
+  ~ProfScope() {
+    if (!h->prof) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, h->stream);
+    h->prof_ev.push_back(a);
+    h->prof_ev.push_back(b);
+    h->prof_id.push_back(id);
+  }
+};
+
+int bt_destroy(bt_handle* h) {
+  if (!h) return BT_OK;
+  prof_clear(h);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  delete h;
+  return BT_OK;
+}
+
+static int copy_in(bt_handle* h, int mem, void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, mem == BT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream);
+  return e == cudaSuccess ? BT_OK : cuda_fail(e, "copy in");
+}
+
+int bt_set_background(bt_handle* h, int mem, const double* rho, const double* T, const double* Ye,
+                      const double* v, const double* alpha, const double* phi, const double* shift,
+                      const double* kappa_a, const double* kappa_s, const double* f_eq) {
+  (void)rho; (void)T; (void)Ye;
+  if (!h || !v || !alpha || !phi || !kappa_a || !kappa_s || !f_eq) return fail(BT_ERR_ARG, "NULL background array");
+  if (mem != BT_MEM_HOST && mem != BT_MEM_DEVICE) return fail(BT_ERR_ARG, "mem");
+  const size_t nz = h->nzone, no = (size_t)h->cfg.n_species * nz * h->cfg.n_eps;
+  if (mem == BT_MEM_HOST) {
+    if (!finite_all(v, 3 * nz) || !finite_all(alpha, nz) || !finite_all(phi, nz) || !finite_all(kappa_a, no) ||
+        !finite_all(kappa_s, no) || !finite_all(f_eq, no))
+      return fail(BT_ERR_BACKGROUND, "non-finite background value");
+    for (size_t z = 0; z < nz; ++z) {
+      if (!(alpha[z] > 0.0) || !(phi[z] > 0.0)) return fail(BT_ERR_BACKGROUND, "alpha and phi must be > 0");
+      double v2 = v[3 * z] * v[3 * z] + v[3 * z + 1] * v[3 * z + 1] + v[3 * z + 2] * v[3 * z + 2];
+      if (!(v2 < 1.0)) return fail(BT_ERR_BACKGROUND, "|v| must be < 1");
+      if (shift && (shift[3 * z] != 0.0 || shift[3 * z + 1] != 0.0 || shift[3 * z + 2] != 0.0))
+        return fail(BT_ERR_BACKGROUND, "non-zero shift is not supported");
+    }
+    for (size_t q = 0; q < no; ++q)
+      if (kappa_a[q] < 0.0 || kappa_s[q] < 0.0) return fail(BT_ERR_BACKGROUND, "negative opacity");
+  }
+  int nxt = h->has_bg ? 1 - h->cur : h->cur;
+  int rc;
+  if ((rc = copy_in(h, mem, h->bg[nxt][0], v, 8 * 3 * nz)) != BT_OK) return rc;
+  if ((rc = copy_in(h, mem, h->bg[nxt][1], alpha, 8 * nz)) != BT_OK) return rc;
+  if ((rc = copy_in(h, mem, h->bg[nxt][2], phi, 8 * nz)) != BT_OK) return rc;
+  if ((rc = copy_in(h, mem, h->ka, kappa_a, 8 * no)) != BT_OK) return rc;
+  if ((rc = copy_in(h, mem, h->ks, kappa_s, 8 * no)) != BT_OK) return rc;
+  if ((rc = copy_in(h, mem, h->fe, f_eq, 8 * no)) != BT_OK) return rc;
+  if (h->has_bg) h->remap_pending = true;
+  h->cur = nxt;
+  h->has_bg = true;
+  return BT_OK;
+}
+
+int bt_set_f(bt_handle* h, int mem, const void* f) {
+  if (!h || !f) return fail(BT_ERR_ARG, "NULL");
+  int rc = copy_in(h, mem, h->f[h->fcur], f, h->fbytes);
+  if (rc == BT_OK) h->remap_pending = false;
+  return rc;
+}
+
+static int check_flag(bt_handle* h) {
+  int flag[4];
+  cudaError_t e = cudaMemcpyAsync(flag, h->st.flag, 16, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  if (flag[0]) return fail(BT_ERR_NUMERIC, "a step produced a non-finite value");
+  return BT_OK;
+}
+
+int bt_get_f(bt_handle* h, int mem, void* f) {
+  if (!h || !f) return fail(BT_ERR_ARG, "NULL");
+  cudaError_t e = cudaMemcpyAsync(f, h->f[h->fcur], h->fbytes,
+                                  mem == BT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_get_f");
+  return check_flag(h);
+}
+
+static void bind_state(bt_handle* h) {
+  bt::State& S = h->st;
+  int old = 1 - h->cur;
+  S.v = h->bg[h->cur][0]; S.al = h->bg[h->cur][1]; S.cf = h->bg[h->cur][2];
+  S.v_old = h->bg[old][0]; S.al_old = h->bg[old][1]; S.cf_old = h->bg[old][2];
+  S.f = h->f[h->fcur];
+  S.f_next = h->f[1 - h->fcur];
+}
+
+int bt_max_dt(bt_handle* h, double cfl, double* dt_out) {
+  if (!h || !dt_out) return fail(BT_ERR_ARG, "NULL");
+  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_max_dt before bt_set_background");
+  bind_state(h);
+  int e = bt::launch_max_rate(h->tb, h->st, h->tmp, h->stream);
+  h->launches += 1;
+  if (e) return cuda_fail((cudaError_t)e, "max_rate");
+  double rate = 0.0;
+  cudaError_t ce = cudaMemcpyAsync(&rate, h->tmp, 8, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "bt_max_dt");
+  if (!(rate > 0.0)) return fail(BT_ERR_STATE, "zero transport rate");
+  *dt_out = cfl / rate;
+  return BT_OK;
+}
+
+int bt_step(bt_handle* h, double dt) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_step before bt_set_background");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BT_ERR_DT, "dt must be positive and finite");
+  bind_state(h);
+  int e;
+  if (h->remap_pending) {
+    ProfScope ps(h, BT_K_TIME_REMAP);
+    e = bt::launch_time_remap(h->tb, h->st, h->mixed, h->stream);
+    h->launches += 1;
+    if (e) return cuda_fail((cudaError_t)e, "time remap");
+    h->remap_pending = false;
+  }
+  {
+    ProfScope ps(h, BT_K_FLUX);
+    e = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, h->stream);
+    h->launches += 1;
+    if (e) return cuda_fail((cudaError_t)e, "flux/collide");
+  }
+  {
+    ProfScope ps(h, BT_K_OUTFLOW);
+    e = bt::launch_accumulate_outflow(h->tb, h->st, h->stream);
+    h->launches += 2;
+    if (e) return cuda_fail((cudaError_t)e, "outflow");
+  }
+  h->fcur = 1 - h->fcur;
+  return BT_OK;
+}
+
+int bt_moments(bt_handle* h, int mem, double* dN, double* dE, double* dP, double* Q_Ye) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  const size_t n = (size_t)h->cfg.n_species * h->nzone;
+  auto kind = mem == BT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  if (dN && e == cudaSuccess) e = cudaMemcpyAsync(dN, h->st.mom_N, 8 * n, kind, h->stream);
+  if (dE && e == cudaSuccess) e = cudaMemcpyAsync(dE, h->st.mom_E, 8 * n, kind, h->stream);
+  if (dP && e == cudaSuccess) e = cudaMemcpyAsync(dP, h->st.mom_P, 8 * 3 * n, kind, h->stream);
+  if (Q_Ye && e == cudaSuccess) e = cudaMemcpyAsync(Q_Ye, h->qye, 8 * h->nzone, kind, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_moments");
+  return check_flag(h);
+}
+
+int bt_totals(bt_handle* h, double* N, double* E, double* N_out, double* E_out) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_totals before bt_set_background");
+  bind_state(h);
+  const int ns = h->cfg.n_species;
+  int e = bt::launch_totals(h->tb, h->st, h->mixed, h->tmp, h->stream);
+  h->launches += 2;
+  if (e) return cuda_fail((cudaError_t)e, "totals");
+  std::vector<double> t(2 * ns), acc(4 * ns);
+  cudaError_t ce = cudaMemcpyAsync(t.data(), h->tmp, 8 * 2 * ns, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(acc.data(), h->st.acc, 8 * 4 * ns, cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "bt_totals");
+  for (int s = 0; s < ns; ++s) {
+    if (N) N[s] = t[2 * s];
+    if (E) E[s] = t[2 * s + 1];
+    if (N_out) N_out[s] = acc[2 * (2 * s)] + acc[2 * (2 * s) + 1];
+    if (E_out) E_out[s] = acc[2 * (2 * s + 1)] + acc[2 * (2 * s + 1) + 1];
+  }
+  return check_flag(h);
+}
+
+int bt_jhk(bt_handle* h, int mem, double* J, double* H, double* K) {
+  if (!h || !J || !H || !K) return fail(BT_ERR_ARG, "NULL");
+  bind_state(h);
+  const size_t n = (size_t)h->cfg.n_species * h->nzone * h->cfg.n_eps;
+  double* d = nullptr;
+  bool tmp = mem != BT_MEM_DEVICE;
+  if (tmp) {
+    cudaError_t ce = cudaMallocAsync(&d, 3 * 8 * n, h->stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "bt_jhk alloc");
+  }
+  double* dJ = tmp ? d : J;
+  double* dH = tmp ? d + n : H;
+  double* dK = tmp ? d + 2 * n : K;
+  int e = bt::launch_jhk(h->tb, h->st, h->mixed, dJ, dH, dK, h->stream);
+  h->launches += 1;
+  if (e) return cuda_fail((cudaError_t)e, "jhk");
+  if (tmp) {
+    cudaMemcpyAsync(J, dJ, 8 * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(H, dH, 8 * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(K, dK, 8 * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+  }
+  cudaError_t ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "bt_jhk");
+  return BT_OK;
+}
+
+int64_t bt_launch_count(const bt_handle* h) { return h ? h->launches : 0; }
+
+int bt_profile(bt_handle* h, int enable) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_profile");
+  prof_clear(h);
+  h->prof = enable != 0;
+  return BT_OK;
+}
+
+int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launches) {
+  if (!h || !total_ms || !launches) return fail(BT_ERR_ARG, "NULL");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_profile_read");
+  double tot = 0.0;
+  int64_t n = 0;
+  for (size_t i = 0; i < h->prof_id.size(); ++i) {
+    if (h->prof_id[i] != kernel) continue;
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  *launches = n;
+  return BT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// bt_internal.h -- data shared by the host side (bt_host.cpp) and the CUDA
+// kernels (bt_kernels.cu) of the transport library.  Not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace bt {
+
+constexpr int kMaxAng = 256;     // angle bins per location
+constexpr int kMaxEps = 64;      // energy groups
+constexpr int kMaxMu = 64;
+constexpr int kMaxFaces = 6;
+
+enum FaceType { F_INTERNAL = 0, F_OUTFLOW_P = 1, F_OUTFLOW_Q = 2, F_REFLECT_Q = 3 };
+enum Axis { AX_R = 0, AX_TH = 1, AX_PH = 2, AX_TIME = 3 };
+
+// Geometry and momentum tables (float64, device pointers), uploaded once.
+struct Tables {
+  int geom, slab, periodic_th, inner_reflect, inner_zero;
+  int n_r, n_th, n_zone, n_s, n_e, n_mu, n_ph, n_ang;
+  double R;            // constant ratio of consecutive group centres
+  double logR;
+  double dphi, dth_col;
+  const double* mu;    // [n_mu] Gauss-Legendre nodes, ascending
+  const double* smu;   // [n_mu] sqrt(1 - mu^2)
+  const double* cph;   // [n_ph] cos Phi_k
+  const double* sph;   // [n_ph] sin Phi_k
+  const double* dOm;   // [n_ang]
+  const double* dGam;  // [n_e]
+  const double* eps;   // [n_e] group centres
+  const double* vol;   // [n_zone]
+  const double* r_e;   // [n_r + 1]
+  const double* r_c;   // [n_r]
+  const double* th_e;  // [n_th + 1]
+  const double* th_c;  // [n_th]
+  const double* area_r;  // [n_th][n_r + 1] radial faces
+  const double* area_t;  // [n_th + 1][n_r] polar faces (column: [1][n_r], the periodic face)
+  const double* area_p;  // [n_th][n_r] azimuthal (periodic) faces
+  const double* G_r;     // [n_th][9]       cell triad -> radial-face triad of row b
+  const double* G_t;     // [n_th + 1][4][9] stencil cell k -> polar face (column: [1][4][9])
+  const double* G_p;     // [n_th][4][9]    periodic image k -> azimuthal face of row b
+  const int* species_kind;
+};
+
+// Per-handle mutable device state.
+struct State {
+  void* f;              // [s][zone][e][ang] (double or float)
+  void* f_next;
+  const double* v;      // [zone][3] current background
+  const double* al;     // [zone]
+  const double* cf;     // [zone] conformal factor
+  const double* v_old;  // previous background (time remap)
+  const double* al_old;
+  const double* cf_old;
+  const double* ka;     // [s][zone][e]
+  const double* ks;
+  const double* fe;
+  double* mom_N;        // [s][zone]
+  double* mom_E;        // [s][zone]
+  double* mom_P;        // [s][zone][3]
+  double* out_N;        // [s][zone] outflow of the last step
+  double* out_E;
+  double* acc;          // [4 * n_s] cumulative N_out, E_out (+ compensation terms)
+  double* red;          // scratch for reductions
+  int* flag;            // [4] error flags (non-finite result, ...)
+  double* qye;          // [zone] lepton-number source term of the last step
+  double phase_norm;    // 1/h^3 factor of the hydro source terms
+};
+
+struct LaunchCfg {
+  int threads;
+  size_t smem_flux;
+  size_t smem_remap;
+};
+
+// Kernel entry points (bt_kernels.cu).  All enqueue on `stream`; return a
+// cudaError_t as int.
+int launch_time_remap(const Tables& T, const State& S, int mixed, void* stream);
+int launch_flux_collide(const Tables& T, const State& S, double dt, int mixed, void* stream);
+int launch_totals(const Tables& T, const State& S, int mixed, double* d_out /*[2*n_s]*/, void* stream);
+int launch_accumulate_outflow(const Tables& T, const State& S, void* stream);
+int launch_max_rate(const Tables& T, const State& S, double* d_rate /*[1]*/, void* stream);
+int launch_jhk(const Tables& T, const State& S, int mixed, double* J, double* H, double* K, void* stream);
+int launch_check_finite(const Tables& T, const State& S, int mixed, void* stream);
+size_t flux_smem_bytes(const Tables& T, int mixed);
+size_t remap_smem_bytes(const Tables& T, int mixed);
+int max_optin_smem();
+
+}  // namespace bt

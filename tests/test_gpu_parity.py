@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs.  FP64 path: relative L1 <= 1e-12 (the bar the transport
+step is held to); mixed path: relative L1 <= 1e-4 after 100 steps."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_02845_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL_MIXED = 1e-4
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2003_02845_gb300 import build, bt
+    build.build()
+    return bt
+
+
+def rel_l1(a, b):
+    return np.abs(np.asarray(a, np.float64) - b).sum() / max(np.abs(b).sum(), 1e-300)
+
+
+def compare_run(orc, bt, prob, n_steps, precision="fp64", tol=TOL64, cfl=0.5):
+    o, dt = orc.run(prob, n_steps=n_steps, cfl=cfl)
+    t, _ = bt.run(prob, precision, n_steps=n_steps, dt=dt)
+    fo, fg = o.get_f(), t.get_f()
+    e = rel_l1(fg, fo)
+    assert e <= tol, "rel-L1(f) = %.3e > %.1e" % (e, tol)
+    # element-wise: every bin within 50 tol of the largest value of its row;
+    # rows below float32's normal range (physically empty high-energy groups)
+    # are held to an absolute bound instead
+    floor = 1e-300 if precision == "fp64" else 1e-30
+    scale = np.maximum(np.abs(fo).max(axis=-1, keepdims=True), floor)
+    assert np.max(np.abs(fg - fo) / scale) <= 50 * tol
+    return o, t, dt
+
+
+# ---------------------------------------------------------------------------
+# FP64 path: element-wise parity on small cases spanning every face type
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [1, 2])
+def test_fp64_column_moving_gr(orc, gpu, seed):
+    p = W.random_column(seed, n_r=11, n_e=5, n_mu=6, n_phi=4, n_s=2)
+    o, t, dt = compare_run(orc, gpu, p, 12)
+    # moments and totals
+    mo, mg = o.moments(), t.moments()
+    for a, b in zip(mg, mo):
+        assert rel_l1(a, b) <= 1e-11
+    No, Ng = o.totals(), t.totals()
+    for a, b in zip(Ng, No):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-300)
+
+
+def test_fp64_column_origin(orc, gpu):
+    # r_edges[0] == 0: zero-area inner face, pyramid zone at the centre
+    p = W.homogeneous_sphere(n_r=13, n_e=3, n_mu=6, n_phi=4, dang=0.25)
+    p.f0 = np.random.default_rng(3).uniform(0, 1, p.f0.shape)
+    compare_run(orc, gpu, p, 10)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_fp64_2d(orc, gpu, seed):
+    p = W.random_2d(seed, n_r=9, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=2)
+    o, t, dt = compare_run(orc, gpu, p, 8)
+    assert math.isclose(t.max_dt(0.5), o.max_dt(0.5), rel_tol=1e-12)
+    No, Ng = o.totals(), t.totals()
+    for a, b in zip(Ng, No):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-300)
+
+
+def test_fp64_2d_origin_and_ragged(orc, gpu):
+    # origin pyramids, poles, odd mu count, angles not a multiple of 32
+    p = W.random_2d(6, n_r=7, n_theta=3, n_e=3, n_mu=5, n_phi=7, n_s=1, r_min=0.0)
+    compare_run(orc, gpu, p, 6)
+
+
+def test_fp64_slab(orc, gpu):
+    p = W.slab_diffusion(kappa_s=30.0, dz=0.02, z_max=0.3, n_mu=6)
+    p.f0 = p.f0 * np.random.default_rng(8).uniform(0.5, 1.5, p.f0.shape)
+    compare_run(orc, gpu, p, 20)
+
+
+def test_fp64_config1_100_steps(orc, gpu):
+    # the homogeneous-sphere configuration at its full size, 100 steps
+    compare_run(orc, gpu, W.config1(), 100)
+
+
+def test_fp64_single_group_single_phi(orc, gpu):
+    p = W.random_column(9, n_r=6, n_e=1, n_mu=4, n_phi=1, n_s=1)
+    compare_run(orc, gpu, p, 5)
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision path
+# ---------------------------------------------------------------------------
+def test_mixed_config1_100_steps(orc, gpu):
+    compare_run(orc, gpu, W.config1(), 100, precision="mixed", tol=TOL_MIXED)
+
+
+def test_mixed_column_moving(orc, gpu):
+    p = W.random_column(11, n_r=10, n_e=5, n_mu=6, n_phi=4, n_s=2)
+    compare_run(orc, gpu, p, 20, precision="mixed", tol=TOL_MIXED)
+
+
+def test_mixed_2d(orc, gpu):
+    p = W.random_2d(12, n_r=8, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=2)
+    compare_run(orc, gpu, p, 10, precision="mixed", tol=TOL_MIXED)
+
+
+# ---------------------------------------------------------------------------
+# Conservation, determinism, degenerate inputs, errors
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-6)])
+def test_gpu_conservation_static(gpu, precision, tol):
+    p = W.random_2d(13, n_r=8, n_theta=4, n_e=3, n_mu=4, n_phi=6, n_s=1)
+    rng = np.random.default_rng(0)
+    for bg in p.backgrounds:
+        bg.v[:] = 0.0
+        bg.alpha[:] = 1.0
+        bg.phi[:] = 1.0
+        bg.kappa_a[:] = 0.0
+        bg.kappa_s[:] = rng.uniform(0, 3, bg.kappa_s.shape)
+    t = gpu.Transport(p, precision)
+    t.set_background(p.backgrounds[0])
+    t.set_f(p.f0)
+    N0, E0, _, _ = t.totals()
+    dt = t.max_dt(0.5)
+    for _ in range(30):
+        t.step(dt)
+    N, E, No, Eo = t.totals()
+    assert np.allclose(N + No, N0, rtol=tol, atol=0)
+    assert np.allclose(E + Eo, E0, rtol=tol, atol=0)
+
+
+def test_gpu_deterministic(gpu):
+    p = W.random_2d(14, n_r=8, n_theta=4, n_e=3, n_mu=4, n_phi=6, n_s=2)
+    a, _ = gpu.run(p, "fp64", n_steps=4, dt=0.01)
+    b, _ = gpu.run(p, "fp64", n_steps=4, dt=0.01)
+    assert np.array_equal(a.get_f(), b.get_f())
+
+
+def test_gpu_zero_state_stays_zero(gpu):
+    p = W.random_column(15, n_r=6, n_e=3, n_mu=4, n_phi=4, n_s=1)
+    for bg in p.backgrounds:
+        bg.kappa_a[:] = 0.0
+    p.f0[:] = 0.0
+    t, _ = gpu.run(p, "fp64", n_steps=3, dt=0.01)
+    assert not np.any(t.get_f())
+
+
+def test_gpu_errors(gpu):
+    p = W.random_column(16, n_r=4, n_e=2, n_mu=2, n_phi=2, n_s=1)
+    t = gpu.Transport(p, "fp64")
+    with pytest.raises(gpu.BtError) as e:
+        t.step(0.1)                              # no background yet
+    assert e.value.code == -6
+    t.set_background(p.backgrounds[0])
+    with pytest.raises(gpu.BtError) as e:
+        t.step(-1.0)
+    assert e.value.code == -3
+    bad = p.backgrounds[0]
+    bad.alpha = bad.alpha.copy()
+    bad.alpha[1] = float("nan")
+    with pytest.raises(gpu.BtError) as e:
+        t.set_background(bad)
+    assert e.value.code == -2
+    q = W.random_column(16, n_r=4, n_e=3, n_mu=2, n_phi=2, n_s=1)
+    q.eps_edges = np.array([1.0, 2.0, 3.0, 5.0])
+    with pytest.raises(gpu.BtError) as e:
+        gpu.Transport(q, "fp64")
+    assert e.value.code == -1
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads: sampled zones against the oracle's subset step
+# ---------------------------------------------------------------------------
+def sampled_parity(orc, bt, prob, precision, tol, zones):
+    o = orc.Oracle(prob)
+    o.set_background(prob.backgrounds[0])
+    o.set_f(prob.f0)
+    dt = o.max_dt(prob.cfl)
+    o.set_background(prob.backgrounds[1])
+    ref = o.step_zones(dt, zones)[:, zones]
+    t = bt.Transport(prob, precision)
+    t.set_background(prob.backgrounds[0])
+    t.set_f(prob.f0)
+    assert math.isclose(t.max_dt(prob.cfl), dt, rel_tol=1e-12)
+    t.set_background(prob.backgrounds[1])
+    t.step(dt)
+    got = t.get_f()[:, zones]
+    e = rel_l1(got, ref)
+    assert e <= tol, "sampled rel-L1 %.3e" % e
+
+
+def _sample_zones(prob, n, seed):
+    rng = np.random.default_rng(seed)
+    z = set(rng.choice(prob.n_zone, n, replace=False).tolist())
+    # boundaries and poles
+    z |= {0, prob.n_r - 1, prob.n_zone - 1, prob.n_zone - prob.n_r}
+    return sorted(z)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
+def test_config3_sampled(orc, gpu, precision, tol):
+    p = W.config3()
+    sampled_parity(orc, gpu, p, precision, tol, _sample_zones(p, 24, 1))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
+def test_config2_full(orc, gpu, precision, tol):
+    p = W.config2()
+    compare_run(orc, gpu, p, 3, precision=precision, tol=tol)
