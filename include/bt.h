@@ -54,7 +54,8 @@ enum {
   BT_ERR_DT = -3,         /* dt <= 0 or not finite */
   BT_ERR_CUDA = -4,       /* a CUDA runtime call failed (message has the CUDA error) */
   BT_ERR_NUMERIC = -5,    /* non-finite value produced by a step */
-  BT_ERR_STATE = -6       /* call order violated (e.g. step before a background) */
+  BT_ERR_STATE = -6,      /* call order violated (e.g. step before a background) */
+  BT_ERR_TIMEOUT = -7     /* a bounded device-side wait (asynchronous copy) gave up */
 };
 
 enum { BT_GEOM_SPHERICAL = 0, BT_GEOM_SLAB = 1 };

@@ -501,6 +501,7 @@ static int check_flag(bt_handle* h) {
   cudaError_t e = cudaMemcpyAsync(flag, h->st.flag, 16, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sync");
+  if (flag[1]) return fail(BT_ERR_TIMEOUT, "a device-side wait for an asynchronous copy gave up");
   if (flag[0]) return fail(BT_ERR_NUMERIC, "a step produced a non-finite value");
   return BT_OK;
 }

@@ -44,8 +44,6 @@ struct FaceDesc {
   double v[3], al, cf;  // face background
 };
 
-__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
 // ---------------------------------------------------------------------------
 // Transformation chain (Sec. 2.2 Eq. transformchain, Sec. 3.2.2-3.2.4)
 // ---------------------------------------------------------------------------
@@ -136,14 +134,6 @@ __device__ __forceinline__ float atan2_t(float y, float x) { return atan2f(y, x)
 __device__ __forceinline__ double exp_t(double x) { return exp(x); }
 __device__ __forceinline__ float exp_t(float x) { return expf(x); }
 
-// Mixed path: interpolation weights are rounded to multiples of 2^-17 so that
-// w_L + w_R == 1 exactly and every product of three weights is exact in
-// float64; the content deposits then conserve number to float64 round-off.
-template <typename T>
-__device__ __forceinline__ T qw(T w) { return w; }
-template <>
-__device__ __forceinline__ float qw<float>(float w) { return rintf(w * 131072.0f) * (1.0f / 131072.0f); }
-
 // Full chain for source angle `ang`: comoving(src) -> Eulerian(src) -> kick
 // -> rotation G (src triad -> dst triad; transposed if gT) -> comoving(dst),
 // then the trilinear weights (Sec. 3.2, Eq. interpolation).
@@ -207,110 +197,254 @@ __device__ void chain_weights(const Tables& tb, const T* s_mu, const Loc<T>& X, 
     kL = ((int)kf) % nph;
     if (kL < 0) kL += nph;
   }
-  w.wmu = qw(wm); w.wph = qw(wp); w.we = qw(we);
+  w.wmu = wm; w.wph = wp; w.we = we;
   w.jL = (short)jL; w.kL = (short)kL; w.m = (short)m; w.pad = 0;
 }
 
 // ---------------------------------------------------------------------------
-// Bucketing of source angles by lower bracket (one warp per remap)
+// Double-float (pairs of float32) for exact-enough sums on the FP32 pipes
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_make(float a) { return ff{a, 0.0f}; }
+// error-free sum of two floats (Knuth's TwoSum)
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return ff{s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, float b) {
+  ff s = two_sum(a.hi, b);
+  float lo = s.lo + a.lo;
+  float hi = s.hi + lo;
+  return ff{hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  float lo = s.lo + (a.lo + b.lo);
+  float hi = s.hi + lo;
+  return ff{hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_shfl_down(ff a, int o) {
+  return ff{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, 1D) into shared memory with an mbarrier.
+// Every wait is bounded: on expiry the kernel raises st.flag[1].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order earlier generic-proxy accesses of shared memory before later
+// async-proxy (TMA) writes to it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr long kWaitLimit = 1L << 22;
+// bounded wait for phase `parity`; returns false (and flags) on expiry
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* flag) {
+  for (long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  flag[1] = 1;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// The remap T applied as two gathers (Sec. 3.2, trilinear weights factorised
+// into an energy part and an angular part):
+//   energy pass:  E[t][b] = sum_i we(t | i, b) src[i][b]   (per source angle b:
+//                 source group i goes to groups clamp(i+m_b) and clamp(i+m_b+1))
+//   angular pass: D[t][b'] = sum_b wa(b' | b) E[t][b]      (per destination angle
+//                 b': the source angles whose bracket contains b')
+// The angular lists are built once per remap and serve every group and
+// species; they are sorted by source angle so the summation order (and the
+// result) is deterministic.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void build_buckets(const Wt<T>* w, int nang, int nph, int nkeys, short* off, short* list, int* cnt) {
-  const int lane = threadIdx.x & 31;
-  for (int k = lane; k < nkeys; k += 32) cnt[k] = 0;
-  __syncwarp();
-  for (int base = 0; base < nang; base += 32) {
-    int bsrc = base + lane;
-    bool act = bsrc < nang;
-    unsigned mask = __ballot_sync(0xffffffffu, act);
-    if (act) {
-      int key = w[bsrc].jL * nph + w[bsrc].kL;
-      unsigned peers = __match_any_sync(mask, key);
-      if (lane == __ffs(peers) - 1) cnt[key] += __popc(peers);
+struct AEnt {
+  T w;     // angular weight wmu * wphi
+  int b;   // source angle
+};
+
+// distinct angular targets of one source angle and their weights
+template <typename T>
+__device__ __forceinline__ int ang_targets(const Wt<T>& W, int nmu, int nph, int* tgt, T* wa) {
+  const int jL = W.jL, kL = W.kL;
+  const int jR = nmu >= 2 ? jL + 1 : jL;
+  const int kR = nph >= 2 ? (kL + 1) % nph : kL;
+  const T mj[2] = {T(1) - W.wmu, W.wmu};
+  const T mk[2] = {T(1) - W.wph, W.wph};
+  int n = 0;
+  for (int dj = 0; dj < 2; ++dj) {
+    int jt = dj ? jR : jL;
+    for (int dk = 0; dk < 2; ++dk) {
+      int kt = dk ? kR : kL;
+      int t = jt * nph + kt;
+      T w = mj[dj] * mk[dk];
+      int q = 0;
+      while (q < n && tgt[q] != t) ++q;
+      if (q == n) { tgt[n] = t; wa[n] = w; ++n; }
+      else wa[q] += w;
     }
-    __syncwarp();
   }
-  // exclusive scan of the counts (chunked per lane, then a warp scan)
-  int per = (nkeys + 31) / 32;
-  int k0 = lane * per, k1 = min(k0 + per, nkeys);
-  int loc = 0;
-  for (int k = k0; k < k1; ++k) loc += cnt[k];
-  int incl = loc;
+  return n;
+}
+
+// Build the angular lists of the remaps whose bit is set in `mask`.
+// off: [nr][na+1], cnt: [nr][na] int scratch, ent: [nr][4 na].  Whole block.
+template <typename T>
+__device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int nmu, int nph, short* off,
+                             int* cnt, AEnt<T>* ent) {
+  const int tid = threadIdx.x;
+  for (int q = tid; q < nr * na; q += kThreads) cnt[q] = 0;
+  __syncthreads();
+  for (int q = tid; q < nr * na; q += kThreads) {
+    int r = q / na, b = q % na;
+    if (!((mask >> r) & 1u)) continue;
+    int tgt[4];
+    T wa[4];
+    int n = ang_targets(W[r * na + b], nmu, nph, tgt, wa);
+    for (int k = 0; k < n; ++k) atomicAdd(&cnt[r * na + tgt[k]], 1);
+  }
+  __syncthreads();
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int r = warp; r < nr; r += kWarps) {
+      if (!((mask >> r) & 1u)) continue;
+      int per = (na + 31) / 32;
+      int k0 = lane * per, k1 = min(k0 + per, na);
+      int loc = 0;
+      for (int k = k0; k < k1; ++k) loc += cnt[r * na + k];
+      int incl = loc;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  int run = incl - loc;
-  for (int k = k0; k < k1; ++k) {
-    int c = cnt[k];
-    off[k] = (short)run;
-    run += c;
-    cnt[k] = 0;
-  }
-  if (lane == 31) off[nkeys] = (short)incl;
-  __syncwarp();
-  for (int base = 0; base < nang; base += 32) {
-    int bsrc = base + lane;
-    bool act = bsrc < nang;
-    unsigned mask = __ballot_sync(0xffffffffu, act);
-    int key = 0;
-    unsigned peers = 0;
-    if (act) {
-      key = w[bsrc].jL * nph + w[bsrc].kL;
-      peers = __match_any_sync(mask, key);
-      int rank = __popc(peers & ((1u << lane) - 1u));
-      list[off[key] + cnt[key] + rank] = (short)bsrc;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int run = incl - loc;
+      for (int k = k0; k < k1; ++k) {
+        int c = cnt[r * na + k];
+        off[r * (na + 1) + k] = (short)run;
+        run += c;
+        cnt[r * na + k] = 0;
+      }
+      if (lane == 31) off[r * (na + 1) + na] = (short)incl;
     }
-    __syncwarp();
-    if (act && lane == __ffs(peers) - 1) cnt[key] += __popc(peers);
-    __syncwarp();
+  }
+  __syncthreads();
+  for (int q = tid; q < nr * na; q += kThreads) {
+    int r = q / na, b = q % na;
+    if (!((mask >> r) & 1u)) continue;
+    int tgt[4];
+    T wa[4];
+    int n = ang_targets(W[r * na + b], nmu, nph, tgt, wa);
+    for (int k = 0; k < n; ++k) {
+      int pos = off[r * (na + 1) + tgt[k]] + atomicAdd(&cnt[r * na + tgt[k]], 1);
+      AEnt<T> e;
+      e.w = wa[k];
+      e.b = b;
+      ent[r * 4 * na + pos] = e;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < nr * na; q += kThreads) {
+    int r = q / na, t = q % na;
+    if (!((mask >> r) & 1u)) continue;
+    AEnt<T>* L = ent + r * 4 * na;
+    int e0 = off[r * (na + 1) + t], e1 = off[r * (na + 1) + t + 1];
+    for (int i = e0 + 1; i < e1; ++i) {
+      AEnt<T> x = L[i];
+      int j = i - 1;
+      while (j >= e0 && L[j].b > x.b) { L[j + 1] = L[j]; --j; }
+      L[j + 1] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Energy pass for column b (source angle b, shift m, upper weight we):
+// E[t] = sum over source groups i with clamp(i+m) == t of (1-we) c_i src[i]
+//      + sum over i with clamp(i+m+1) == t of we c_i src[i],
+// with c_i = cang * rowf[i] (rowf == nullptr: c_i = 1), which folds the
+// conversion of f into content density into the pass.
+template <typename T, typename A>
+__device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, int b, int m, T we, const T* src, T* E,
+                                              T cang = T(1), const T* rowf = nullptr) {
+  const A wl = (A)cang * (A(1) - (A)we), wr = (A)cang * (A)we;
+  for (int t = gc; t < ne; t += nch) {
+    A acc = A(0);
+    if (t > 0 && t < ne - 1) {
+      int iL = t - m, iR = t - m - 1;
+      if (iL >= 0 && iL < ne) acc += wl * (rowf ? (A)rowf[iL] : A(1)) * (A)src[iL * na + b];
+      if (iR >= 0 && iR < ne) acc += wr * (rowf ? (A)rowf[iR] : A(1)) * (A)src[iR * na + b];
+    } else {
+      int lo = (t == 0) ? 0 : t - m;
+      int hi = (t == ne - 1) ? ne - 1 : t - m;
+      lo = max(lo, 0); hi = min(hi, ne - 1);
+      for (int i = lo; i <= hi; ++i) acc += wl * (rowf ? (A)rowf[i] : A(1)) * (A)src[i * na + b];
+      lo = (t == 0) ? 0 : t - m - 1;
+      hi = (t == ne - 1) ? ne - 1 : t - m - 1;
+      lo = max(lo, 0); hi = min(hi, ne - 1);
+      for (int i = lo; i <= hi; ++i) acc += wr * (rowf ? (A)rowf[i] : A(1)) * (A)src[i * na + b];
+    }
+    E[t * na + b] = (T)acc;
   }
 }
 
-// Gather of one destination bin (ip, bp) of T[src]: sum over source angles in
-// the candidate buckets, each with its clamped two-group energy split.
-template <typename T, typename Acc>
-__device__ __forceinline__ Acc gather_bin(int ip, int bp, int ne, int nang, int nmu, int nph, const T* src,
-                                         const Wt<T>* w, const short* off, const short* list) {
-  const int jp = bp / nph, kp = bp % nph;
-  const int jmax = nmu >= 2 ? nmu - 2 : 0;
-  Acc acc = Acc(0);
-  int kc[2];
-  int nk = 1;
-  kc[0] = kp;
-  if (nph > 1) { kc[1] = (kp - 1 + nph) % nph; nk = 2; }
-  for (int dj = 0; dj < 2; ++dj) {
-    int jL = jp - 1 + dj;
-    if (jL < 0 || jL > jmax) continue;
-    for (int dk = 0; dk < nk; ++dk) {
-      int key = jL * nph + kc[dk];
-      int e0 = off[key], e1 = off[key + 1];
-      for (int q = e0; q < e1; ++q) {
-        int bs = list[q];
-        const Wt<T> W = w[bs];
-        T wmu = (jp == W.jL ? T(1) - W.wmu : T(0)) + (jp == W.jL + 1 ? W.wmu : T(0));
-        int kR = nph > 1 ? (W.kL + 1) % nph : W.kL;
-        T wph = (kp == W.kL ? T(1) - W.wph : T(0)) + (kp == kR ? W.wph : T(0));
-        Acc wa = (Acc)wmu * (Acc)wph;
-        if (wa == Acc(0)) continue;
-        int m = W.m;
-        Acc se = Acc(0);
-        // left target clamp(i+m) == ip, right target clamp(i+m+1) == ip
-        int lo = (ip == 0) ? 0 : ip - m;
-        int hi = (ip == ne - 1) ? ne - 1 : ip - m;
-        lo = max(lo, 0); hi = min(hi, ne - 1);
-        Acc wl = Acc(1) - (Acc)W.we;
-        for (int i = lo; i <= hi; ++i) se += wl * (Acc)src[i * nang + bs];
-        lo = (ip == 0) ? 0 : ip - m - 1;
-        hi = (ip == ne - 1) ? ne - 1 : ip - m - 1;
-        lo = max(lo, 0); hi = min(hi, ne - 1);
-        for (int i = lo; i <= hi; ++i) se += (Acc)W.we * (Acc)src[i * nang + bs];
-        acc += wa * se;
-      }
+// Angular pass for destination angle bp over the rows of this thread:
+// out(t) = sum_e w_e E[t][b_e]; the list (at most 8 entries kept in registers,
+// longer lists streamed) is read once for all rows.
+template <typename T, typename A, typename Out>
+__device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int e0, int e1, const AEnt<T>* ent,
+                                             const T* E, Out out) {
+  const int n = e1 - e0;
+  if (n <= 8) {
+    T w[8];
+    int bb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k < n) { w[k] = ent[e0 + k].w; bb[k] = ent[e0 + k].b; }
+      else { w[k] = T(0); bb[k] = 0; }
+    }
+    for (int t = gc; t < ne; t += nch) {
+      const T* Er = E + t * na;
+      A acc = A(0);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < n) acc += (A)w[k] * (A)Er[bb[k]];
+      out(t, acc);
+    }
+  } else {
+    for (int t = gc; t < ne; t += nch) {
+      const T* Er = E + t * na;
+      A acc = A(0);
+      for (int k = e0; k < e1; ++k) acc += (A)ent[k].w * (A)Er[ent[k].b];
+      out(t, acc);
     }
   }
-  return acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -404,62 +538,140 @@ __device__ bool make_face(const Tables& tb, const State& st, int a, int b, int f
   return true;
 }
 
-__device__ __forceinline__ int nkeys_of(const Tables& tb) { return (tb.n_mu >= 2 ? tb.n_mu - 1 : 1) * tb.n_ph; }
+__device__ __forceinline__ double pow6(double x) {
+  double x2 = x * x;
+  return x2 * x2 * x2;
+}
+
+// Face constants in the arithmetic type (staged once per face).
+template <typename T>
+struct FaceT {
+  T xs, dx, area, al, cf, c6;
+  T sP, sQ;                 // xs - x1, xs - x2
+  T rdx, rdl0, rdl1, rdl2;  // reciprocals of dx and the stencil spacings
+  T c6k[4];                 // phi^6 of the stencil cells
+};
+
+constexpr int kFaces = 5;
+
+// dN accumulator type: float64 for the FP64 path; float for the mixed path,
+// whose per-zone content totals are tracked exactly (double-float) and
+// restored before the collision solve.
+template <typename T>
+struct DNT;
+template <>
+struct DNT<double> { using type = double; };
+template <>
+struct DNT<float> { using type = float; };
 
 // Shared-memory carve-up of the flux kernel.
 template <typename T>
 struct FluxSmem {
-  double* dN;      // [ns][ne][nang]
-  T* src;          // [ne][nang]
-  T* g;            // [4][ne][nang]
-  Wt<T>* W;        // [6][nang]
-  short* off;      // [6][nkeys + 1]
-  short* list;     // [6][nang]
-  int* cnt;        // [6][nkeys]
-  T* u0s;          // [nang] face
-  T* vns;          // [nang]
-  T* rowJ;         // [ne]
-  T* kaS; T* ksS; T* feS; T* wP; T* wQ;  // [ne]
-  T* mu;           // [nmu]
+  typename DNT<T>::type* dN;  // [ns][ne][nang]
   double* zu0;     // [nang] own zone u^0
+  double* ztau;    // [nang] alpha dt / u^0
+  double* zcn;     // [nang] 1/(phi^6 dV u^0 dOmega)
   double* zrow;    // [ns][ne][5] collision moment partials
+  double* wr_r;    // [kWarps][nang] f* of the warp's collision row   (aliases buf)
+  double* wr_i;    // [kWarps][nang] 1/D per warp row                 (aliases buf)
   double* red;     // [kWarps * 2]
   double* tally;   // [ns][2] outflow N, E of this zone
-  FaceDesc* F;
+  double* corr;    // [ns] exact-total correction of dN (mixed)
+  int* corr_at;    // [ns]
+  ff* dtot;        // [ns] exact total of the deposits (mixed)
+  ff* redf;        // [kWarps]
+  float* rkey;     // [kWarps]
+  int* ridx;       // [kWarps]
+  unsigned long long* bar;  // mbarrier of the stencil copies
+  T* buf;          // [8][ne][nang]: 4 stencil/g buffers, 4 work buffers
+  Wt<T>* W;        // [6][nang]   (aliases the work buffers)
+  int* cnt;        // [6][nang]   (aliases the work buffers)
+  AEnt<T>* ent;    // [6][4 nang]
+  short* off;      // [6][nang + 1]
+  T* n0; T* n1; T* n2;  // [nang] direction components
+  T* dOm;          // [nang]
+  T* dGam;         // [ne]
+  T* rdGam;        // [ne] 1/dGamma
+  T* mu;           // [nmu]
+  T* u0s;          // [nang] face
+  T* vns;          // [nang]
+  T* cs;           // [nang] 1/(phi_s^6 u0_s dOmega)
+  T* taus;         // [nang] (dt/2) alpha_s / u0_s
+  T* vdx;          // [nang] (dt/2) v_s / dx
+  T* rowJ;         // [ne]
+  T* kaS; T* ksS; T* feS; T* wP; T* wQ;  // [ne]
+  FaceDesc* F;     // [kFaces]
+  FaceT<T>* FT;    // [kFaces]
 };
 
 template <typename T>
-__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, int nph, FluxSmem<T>* s, unsigned char* base) {
+__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, FluxSmem<T>* s, unsigned char* base) {
   size_t o = 0;
   const int nbin = ne * nang;
-  const int nkeys = (nmu >= 2 ? nmu - 1 : 1) * nph;
 #define BT_TAKE(ptr, type, count)                              \
   do {                                                         \
     o = (o + 15) & ~size_t(15);                                \
     if (s) s->ptr = reinterpret_cast<type*>(base + o);         \
     o += sizeof(type) * (size_t)(count);                       \
   } while (0)
-  BT_TAKE(dN, double, (size_t)ns * nbin);
+  BT_TAKE(bar, unsigned long long, 2);
+  BT_TAKE(dN, typename DNT<T>::type, (size_t)ns * nbin);
   BT_TAKE(zu0, double, nang);
+  BT_TAKE(ztau, double, nang);
+  BT_TAKE(zcn, double, nang);
   BT_TAKE(zrow, double, (size_t)ns * ne * 5);
   BT_TAKE(red, double, kWarps * 2);
   BT_TAKE(tally, double, ns * 2);
-  BT_TAKE(src, T, nbin);
-  BT_TAKE(g, T, 4 * nbin);
-  BT_TAKE(W, Wt<T>, 6 * nang);
+  BT_TAKE(corr, double, ns);
+  BT_TAKE(corr_at, int, ns);
+  BT_TAKE(dtot, ff, ns);
+  BT_TAKE(redf, ff, kWarps);
+  BT_TAKE(rkey, float, kWarps);
+  BT_TAKE(ridx, int, kWarps);
+  {
+    // buf = 4 stencil buffers followed by 4 work buffers.  The remap weights
+    // and list counters live only until the lists are built, when the work
+    // buffers are idle; the collision scratch only after the last face.
+    size_t o_b = (o + 15) & ~size_t(15);
+    size_t stencil = sizeof(T) * (size_t)4 * nbin;
+    size_t o_work = o_b + stencil;
+    size_t o_c = (o_work + sizeof(Wt<T>) * (size_t)6 * nang + 15) & ~size_t(15);
+    size_t need_work = sizeof(T) * (size_t)4 * nbin;
+    size_t need_wc = o_c + sizeof(int) * (size_t)6 * nang - o_work;
+    size_t need_col = sizeof(double) * (size_t)2 * kWarps * nang;
+    size_t tot = stencil + (need_work > need_wc ? need_work : need_wc);
+    if (need_col > tot) tot = need_col;
+    if (s) {
+      s->buf = reinterpret_cast<T*>(base + o_b);
+      s->W = reinterpret_cast<Wt<T>*>(base + o_work);
+      s->cnt = reinterpret_cast<int*>(base + o_c);
+      s->wr_r = reinterpret_cast<double*>(base + o_b);
+      s->wr_i = reinterpret_cast<double*>(base + o_b) + (size_t)kWarps * nang;
+    }
+    o = o_b + tot;
+  }
+  BT_TAKE(ent, AEnt<T>, 6 * 4 * nang);
+  BT_TAKE(off, short, 6 * (nang + 1));
+  BT_TAKE(n0, T, nang);
+  BT_TAKE(n1, T, nang);
+  BT_TAKE(n2, T, nang);
+  BT_TAKE(dOm, T, nang);
+  BT_TAKE(dGam, T, ne);
+  BT_TAKE(rdGam, T, ne);
+  BT_TAKE(mu, T, nmu);
   BT_TAKE(u0s, T, nang);
   BT_TAKE(vns, T, nang);
+  BT_TAKE(cs, T, nang);
+  BT_TAKE(taus, T, nang);
+  BT_TAKE(vdx, T, nang);
   BT_TAKE(rowJ, T, ne);
   BT_TAKE(kaS, T, ne);
   BT_TAKE(ksS, T, ne);
   BT_TAKE(feS, T, ne);
   BT_TAKE(wP, T, ne);
   BT_TAKE(wQ, T, ne);
-  BT_TAKE(mu, T, nmu);
-  BT_TAKE(off, short, 6 * (nkeys + 1));
-  BT_TAKE(list, short, 6 * nang);
-  BT_TAKE(cnt, int, 6 * nkeys);
-  BT_TAKE(F, FaceDesc, 1);
+  BT_TAKE(F, FaceDesc, kFaces);
+  BT_TAKE(FT, FaceT<T>, kFaces);
 #undef BT_TAKE
   return (o + 15) & ~size_t(15);
 }
@@ -485,46 +697,168 @@ __device__ __forceinline__ double block_sum2(double v0, double v1, double* red, 
   if (lane == 0) { red[2 * w] = v0; red[2 * w + 1] = v1; }
   __syncthreads();
   double s0 = 0.0, s1 = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kWarps; ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
-  }
+  for (int i = 0; i < kWarps; ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
   __syncthreads();
   out1 = s1;
   return s0;
 }
 
+// deterministic block sum of double-floats (result in every thread)
+__device__ __forceinline__ ff block_sum_ff(ff v, ff* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_down(v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  ff t = red[0];
+  for (int i = 1; i < kWarps; ++i) t = ff_add(t, red[i]);
+  __syncthreads();
+  return t;
+}
+
+// block argmax of key >= 0 (ties -> smallest index); result in every thread
+__device__ __forceinline__ int block_argmax(float key, int idx, float* rk, int* ri) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float k2 = __shfl_down_sync(0xffffffffu, key, o);
+    int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+    if (k2 > key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { rk[w] = key; ri[w] = idx; }
+  __syncthreads();
+  float bk = rk[0];
+  int bi = ri[0];
+  for (int i = 1; i < kWarps; ++i)
+    if (rk[i] > bk || (rk[i] == bk && ri[i] < bi)) { bk = rk[i]; bi = ri[i]; }
+  __syncthreads();
+  return bi;
+}
+
+// Conservation correction of a float gather: the values dep[0..n) must sum
+// to `target`; returns the residual of their float rounding (as a
+// double-float) and in *at the index of the largest |dep| that takes it.
+__device__ __forceinline__ ff conservation_residual(const float* dep, int n, ff target, ff* redf, float* rk, int* ri,
+                                                    int* at) {
+  ff part = ff{0.0f, 0.0f};
+  float bk = -1.0f;
+  int bi = 0x7fffffff;
+  for (int q = threadIdx.x; q < n; q += kThreads) {
+    part = ff_add(part, dep[q]);
+    float k = fabsf(dep[q]);
+    if (k > bk) { bk = k; bi = q; }
+  }
+  ff tot = block_sum_ff(part, redf);
+  *at = block_argmax(bk, bi, rk, ri);
+  return ff_add(target, ff_neg(tot));
+}
+__device__ __forceinline__ ff conservation_residual(const double*, int, ff, ff*, float*, int*, int* at) {
+  *at = -1;
+  return ff{0.0f, 0.0f};
+}
+
+template <typename T>
+struct StoreG {   // g = D / (phi_s^6 u0_s dGamma dOmega) in the face frame
+  T* dst; const T* rdGam; T cs; int na, b;
+  __device__ void operator()(int t, T acc) const { dst[t * na + b] = acc * rdGam[t] * cs; }
+};
+template <typename T>
+struct StoreT {
+  T* dst; int na, b;
+  __device__ void operator()(int t, T acc) const { dst[t * na + b] = acc; }
+};
+
 // ---------------------------------------------------------------------------
 // Fused face fluxes + collision of one zone (Sec. 3.3, 3.5, 3.4)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, double dt) {
+struct AddDN {   // dN += sign * T[F]
+  typename DNT<T>::type* dn; int na, b; T sign;
+  __device__ void operator()(int t, T acc) const { dn[t * na + b] += (typename DNT<T>::type)(sign * acc); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_collide(Tables tb, State st, double dt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  using DN = typename DNT<T>::type;
   FluxSmem<T> S;
-  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, &S, smem_raw);
+  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, &S, smem_raw);
   const int zone = blockIdx.x;
   const int a = zone % tb.n_r, b = zone / tb.n_r;
   const int NE = tb.n_e, NA = tb.n_ang, NS = tb.n_s, NPH = tb.n_ph, NMU = tb.n_mu;
   const int nbin = NE * NA;
-  const int nkeys = nkeys_of(tb);
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  const int nch = kThreads / NA > 0 ? kThreads / NA : 1;   // row chunks
+  const int gb = tid % NA, gc = tid / NA;                   // this thread's angle, chunk
+  const bool gact = tid < nch * NA;
   const T* fin = reinterpret_cast<const T*>(st.f);
   T* fout = reinterpret_cast<T*>(st.f_next);
+  T* const SRC = S.buf;              // [4] stencil f rows (TMA), then g (face f values)
+  T* const EB = S.buf + 4 * nbin;    // [4] work buffers
+  const unsigned rowbytes = (unsigned)(sizeof(T) * (size_t)nbin);
+  const bool use_tma = (rowbytes % 16u) == 0u;
+  unsigned tphase = 0;               // parity of the next mbarrier phase to wait for
 
-  for (int q = tid; q < NS * nbin; q += kThreads) S.dN[q] = 0.0;
+  for (int q = tid; q < NS * nbin; q += kThreads) S.dN[q] = DN(0);
   for (int q = tid; q < NMU; q += kThreads) S.mu[q] = (T)tb.mu[q];
+  for (int q = tid; q < NA; q += kThreads) {
+    int j = q / NPH, k = q % NPH;
+    S.n0[q] = (T)tb.mu[j];
+    S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
+    S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
+    S.dOm[q] = (T)tb.dOm[q];
+  }
+  for (int q = tid; q < NE; q += kThreads) { S.dGam[q] = (T)tb.dGam[q]; S.rdGam[q] = (T)(1.0 / tb.dGam[q]); }
   for (int q = tid; q < NS * 2; q += kThreads) S.tally[q] = 0.0;
+  for (int q = tid; q < NS; q += kThreads) S.dtot[q] = ff{0.0f, 0.0f};
+  if (tid == 0) mbar_init(S.bar, 1);
+  const int nface = tb.slab ? 2 : kFaces;
+  if (tid < nface) {
+    FaceDesc& Fd = S.F[tid];
+    if (!make_face(tb, st, a, b, tid, Fd)) {
+      Fd.type = -1;
+    } else {
+      FaceT<T>& ft = S.FT[tid];
+      ft.xs = (T)Fd.xs; ft.dx = (T)Fd.dx; ft.area = (T)Fd.area;
+      ft.al = (T)Fd.al; ft.cf = (T)Fd.cf; ft.c6 = (T)pow6(Fd.cf);
+      ft.sP = (T)(Fd.xs - Fd.x[1]); ft.sQ = (T)(Fd.xs - Fd.x[2]);
+      ft.rdx = (T)(1.0 / Fd.dx);
+      ft.rdl0 = Fd.z[0] >= 0 ? (T)(1.0 / (Fd.x[1] - Fd.x[0])) : T(0);
+      ft.rdl1 = (T)(1.0 / (Fd.x[2] - Fd.x[1]));
+      ft.rdl2 = Fd.z[3] >= 0 ? (T)(1.0 / (Fd.x[3] - Fd.x[2])) : T(0);
+      for (int k = 0; k < 4; ++k) ft.c6k[k] = Fd.z[k] >= 0 ? (T)pow6(st.cf[Fd.z[k]]) : T(0);
+    }
+  }
   __syncthreads();
 
-  const int nface = tb.slab ? 2 : 5;
-  for (int fidx = 0; fidx < nface; ++fidx) {
-    if (tid == 0) {
-      bool ok = make_face(tb, st, a, b, fidx, *S.F);
-      if (!ok) S.F->type = -1;
-    }
-    __syncthreads();
-    const FaceDesc& F = *S.F;
-    if (F.type < 0) { __syncthreads(); continue; }
+  // stencil rows of (face fi, species si) into SRC: bulk copies by thread 0
+  auto issue = [&](int fi, int si) {
+    if (!use_tma || tid != 0) return;
+    const FaceDesc& Fn = S.F[fi];
+    unsigned bytes = 0;
+    for (int k = 0; k < 4; ++k) if (Fn.z[k] >= 0) bytes += rowbytes;
+    fence_proxy_async();
+    mbar_expect_tx(S.bar, bytes);
+    for (int k = 0; k < 4; ++k)
+      if (Fn.z[k] >= 0) tma_load_1d(SRC + k * nbin, fin + ((size_t)si * tb.n_zone + Fn.z[k]) * nbin, rowbytes, S.bar);
+  };
+  // next existing face after fi (or nface)
+  auto next_face = [&](int fi) {
+    int f = fi + 1;
+    while (f < nface && S.F[f].type < 0) ++f;
+    return f;
+  };
+  int first = next_face(-1);
+  if (first < nface) issue(first, 0);
+
+  for (int fidx = first; fidx < nface; fidx = next_face(fidx)) {
+    const FaceDesc& F = S.F[fidx];
+    const FaceT<T>& ft = S.FT[fidx];
+    unsigned mask = 0;
+    for (int k = 0; k < 4; ++k) if (F.z[k] >= 0) mask |= 1u << k;
+    if (F.own & 1) mask |= 1u << 4;
+    if (F.own & 2) mask |= 1u << 5;
 
     // --- weights of the six remaps: slots 0..3 -> face, face -> slot 1, face -> slot 2
     {
@@ -532,9 +866,8 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
       make_loc(Ls, F.v, F.al, F.cf);
       for (int q = tid; q < 6 * NA; q += kThreads) {
         int r = q / NA, ang = q % NA;
+        if (!((mask >> r) & 1u)) continue;
         int slot = r < 4 ? r : r - 3;
-        bool need = r < 4 ? (F.z[slot] >= 0) : ((r == 4 && (F.own & 1)) || (r == 5 && (F.own & 2)));
-        if (!need) continue;
         int zz = F.z[slot];
         Loc<T> Lc;
         make_loc(Lc, st.v + 3 * zz, st.al[zz], st.cf[zz]);
@@ -545,24 +878,40 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
       }
       // face bins: Eulerian energy factor and normal coordinate velocity
       for (int ang = tid; ang < NA; ang += kThreads) {
-        const int j = ang / NPH, k = ang % NPH;
-        T n[3] = {S.mu[j], (T)tb.smu[j] * (T)tb.cph[k], (T)tb.smu[j] * (T)tb.sph[k]};
+        T n[3] = {S.n0[ang], S.n1[ang], S.n2[ang]};
         T e, p[3];
         boost_fwd(Ls, n, e, p);
         S.u0s[ang] = e;
-        S.vns[ang] = Ls.al / (Ls.cf * Ls.cf) * p[F.axis] / e;
+        T vn = Ls.al / (Ls.cf * Ls.cf) * p[F.axis] / e;
+        S.vns[ang] = vn;
+        S.cs[ang] = T(1) / (ft.c6 * e * S.dOm[ang]);
+        S.taus[ang] = T(0.5) * (T)dt * ft.al / e;
+        S.vdx[ang] = T(0.5) * (T)dt * vn * ft.rdx;
       }
     }
     __syncthreads();
-    if (warp < 6) {
-      int r = warp;
-      int slot = r < 4 ? r : r - 3;
-      bool need = r < 4 ? (F.z[slot] >= 0) : ((r == 4 && (F.own & 1)) || (r == 5 && (F.own & 2)));
-      if (need) build_buckets(S.W + r * NA, NA, NPH, nkeys, S.off + r * (nkeys + 1), S.list + r * NA, S.cnt + r * nkeys);
+    // energy-pass parameters of this thread's column for the six remaps,
+    // and the density factor of its angle for the four stencil cells
+    int em[6];
+    T ew[6], cang[4];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      if (gact && ((mask >> r) & 1u)) { em[r] = S.W[r * NA + gb].m; ew[r] = S.W[r * NA + gb].we; }
+      else { em[r] = 0; ew[r] = T(0); }
     }
-    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cang[k] = T(0);
+      if (gact && F.z[k] >= 0) {
+        const double* v = st.v + 3 * F.z[k];
+        const T vx = (T)v[0], vy = (T)v[1], vz = (T)v[2];
+        const T g = T(1) / sqrt(T(1) - (vx * vx + vy * vy + vz * vz));
+        const T u0 = g * (T(1) + (vx * S.n0[gb] + vy * S.n1[gb] + vz * S.n2[gb]));
+        cang[k] = ft.c6k[k] * u0 * S.dOm[gb];
+      }
+    }
+    build_alists(S.W, 6, mask, NA, NMU, NPH, S.off, S.cnt, S.ent);   // synchronises
 
-    const T c6s = (T)pow(F.cf, 6.0);
     for (int s = 0; s < NS; ++s) {
       // face opacities and flux-switch weights per group [R-10, R-12b]
       if (F.type == F_INTERNAL) {
@@ -573,52 +922,82 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
           S.kaS[i] = (T)(0.5 * (kaP + kaQ));
           S.ksS[i] = (T)(0.5 * (ksP + ksQ));
           S.feS[i] = (T)(0.5 * (st.fe[oP] + st.fe[oQ]));
-          S.wP[i] = exp_t((T)(-(kaP + ksP)) * (T)F.dx);
-          S.wQ[i] = exp_t((T)(-(kaQ + ksQ)) * (T)F.dx);
+          S.wP[i] = exp_t((T)(-(kaP + ksP)) * ft.dx);
+          S.wQ[i] = exp_t((T)(-(kaQ + ksQ)) * ft.dx);
         }
       }
-      // stencil contents remapped into the face frame: g_k = T_{k->s}[n_k]
-      for (int slot = 0; slot < 4; ++slot) {
-        const int zz = F.z[slot];
-        if (zz < 0) continue;
-        Loc<T> Lc;
-        make_loc(Lc, st.v + 3 * zz, st.al[zz], st.cf[zz]);
-        const T c6 = (T)pow(st.cf[zz], 6.0);
-        const T* fz = fin + ((size_t)s * tb.n_zone + zz) * nbin;
-        for (int q = tid; q < nbin; q += kThreads) {
-          int i = q / NA, ang = q % NA;
-          int j = ang / NPH, k = ang % NPH;
-          T nv = Lc.v[0] * S.mu[j] + (Lc.v[1] * (T)tb.cph[k] + Lc.v[2] * (T)tb.sph[k]) * (T)tb.smu[j];
-          T u0 = Lc.g * (T(1) + nv);
-          S.src[q] = c6 * u0 * (T)tb.dGam[i] * (T)tb.dOm[ang] * fz[q];
+      // stencil rows of this species (f as stored)
+      if (use_tma) {
+        bool ok = mbar_wait(S.bar, tphase, st.flag);
+        tphase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+          // give the copy in flight a second bounded chance, then stop
+          if (tid == 0) mbar_wait(S.bar, tphase ^ 1u, st.flag);
+          __syncthreads();
+          return;
         }
-        __syncthreads();
-        T* gk = S.g + slot * nbin;
-        const Wt<T>* W = S.W + slot * NA;
-        const short* off = S.off + slot * (nkeys + 1);
-        const short* lst = S.list + slot * NA;
-        for (int q = tid; q < nbin; q += kThreads) {
-          int ip = q / NA, bp = q % NA;
-          T d = gather_bin<T, T>(ip, bp, NE, NA, NMU, NPH, S.src, W, off, lst);
-          gk[q] = d / (c6s * S.u0s[bp] * (T)tb.dGam[ip] * (T)tb.dOm[bp]);
+      } else {
+        if (gact) {
+          for (int k = 0; k < 4; ++k) {
+            const int zz = F.z[k];
+            if (zz < 0) continue;
+            const T* fz = fin + ((size_t)s * tb.n_zone + zz) * nbin;
+            for (int i = gc; i < NE; i += nch) SRC[k * nbin + i * NA + gb] = fz[i * NA + gb];
+          }
         }
         __syncthreads();
       }
-      // Lax-Wendroff half step with implicit collision: J per group (one warp per row)
-      const T hdt = T(0.5) * (T)dt;
+      // energy pass of the stencil remaps (content density folded in)
+      if (gact) {
+#pragma unroll
+        for (int slot = 0; slot < 4; ++slot)
+          if (F.z[slot] >= 0)
+            energy_column<T, T>(gc, nch, NE, NA, gb, em[slot], ew[slot], SRC + slot * nbin, EB + slot * nbin,
+                                cang[slot], S.dGam);
+      }
+      __syncthreads();
+      // angular pass: g_k = T_{k->s}[n_k] as face distribution (into SRC)
+      if (gact) {
+        const T csb = S.cs[gb];
+        for (int slot = 0; slot < 4; ++slot) {
+          if (F.z[slot] < 0) continue;
+          const short* off = S.off + slot * (NA + 1);
+          StoreG<T> st_g{SRC + slot * nbin, S.rdGam, csb, NA, gb};
+          angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
+        }
+      }
+      __syncthreads();
+      const T* G0 = SRC;
+      const T* G1 = SRC + nbin;
+      const T* G2 = SRC + 2 * nbin;
+      const T* G3 = SRC + 3 * nbin;
+      T* RD = EB;                 // r / D
+      T* FL = EB + nbin;          // flux content
+      T* ID = EB + 2 * nbin;      // 1 / D
+      // Lax-Wendroff half step with implicit collision [R-10]: per bin
+      // r = (g1+g2)/2 - (dt/2) v (g2-g1)/dx + tau ka feq, D = 1 + (ka+ks) tau
       if (F.type == F_INTERNAL) {
+        if (gact) {
+          const T tau = S.taus[gb], vdx = S.vdx[gb];
+          for (int i = gc; i < NE; i += nch) {
+            const int q = i * NA + gb;
+            const T g1 = G1[q], g2 = G2[q];
+            const T r = T(0.5) * (g1 + g2) - vdx * (g2 - g1) + tau * S.kaS[i] * S.feS[i];
+            const T iD = T(1) / (T(1) + (S.kaS[i] + S.ksS[i]) * tau);
+            RD[q] = r * iD;
+            ID[q] = iD;
+          }
+        }
+        __syncthreads();
+        // J per group (Sherman-Morrison closed form; one warp per row)
         for (int i = warp; i < NE; i += kWarps) {
           T sr = T(0), s1 = T(0);
-          const T ka = S.kaS[i], ks = S.ksS[i], fe = S.feS[i];
+          const T ka = S.kaS[i];
           for (int ang = lane; ang < NA; ang += 32) {
-            int q = i * NA + ang;
-            T g1 = S.g[nbin + q], g2 = S.g[2 * nbin + q];
-            T tau = hdt * (T)F.al / S.u0s[ang];
-            T r = T(0.5) * (g1 + g2) - hdt * S.vns[ang] * (g2 - g1) / (T)F.dx + tau * ka * fe;
-            T D = T(1) + (ka + ks) * tau;
-            T dom = (T)tb.dOm[ang];
-            sr += dom * r / D;
-            s1 += dom * (T(1) + ka * tau) / D;
+            const int q = i * NA + ang;
+            const T dom = S.dOm[ang];
+            sr += dom * RD[q];
+            s1 += dom * ID[q] * (T(1) + ka * S.taus[ang]);
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
@@ -630,71 +1009,120 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
         __syncthreads();
       }
       // interface state (blend of LW and MC upwind) and flux content per face bin
-      for (int q = tid; q < nbin; q += kThreads) {
-        int i = q / NA, ang = q % NA;
-        T vn = S.vns[ang];
-        T fs;
-        if (F.type == F_INTERNAL) {
-          T g0 = S.g[q], g1 = S.g[nbin + q], g2 = S.g[2 * nbin + q], g3 = S.g[3 * nbin + q];
-          const T ka = S.kaS[i], ks = S.ksS[i], fe = S.feS[i];
-          T tau = hdt * (T)F.al / S.u0s[ang];
-          T r = T(0.5) * (g1 + g2) - hdt * vn * (g2 - g1) / (T)F.dx + tau * ka * fe;
-          T D = T(1) + (ka + ks) * tau;
-          T flw = (r + ks * tau * S.rowJ[i]) / D;
-          T fu, w;
-          if (vn >= T(0)) {
-            T sl = T(0);
-            if (F.z[0] >= 0) sl = mc_limiter((g1 - g0) / (T)(F.x[1] - F.x[0]), (g2 - g1) / (T)(F.x[2] - F.x[1]));
-            fu = g1 + sl * (T)(F.xs - F.x[1]);
-            w = S.wP[i];
-          } else {
-            T sl = T(0);
-            if (F.z[3] >= 0) sl = mc_limiter((g2 - g1) / (T)(F.x[2] - F.x[1]), (g3 - g2) / (T)(F.x[3] - F.x[2]));
-            fu = g2 + sl * (T)(F.xs - F.x[2]);
-            w = S.wQ[i];
+      ff sumF = ff{0.0f, 0.0f};
+      double tn = 0.0, te = 0.0;
+      const bool outflow = F.type == F_OUTFLOW_P || F.type == F_OUTFLOW_Q;
+      if (gact) {
+        const T vn = S.vns[gb];
+        const T fang = (T)dt * ft.area * ft.c6 * S.u0s[gb] * vn * S.dOm[gb];
+        const int jj = gb / NPH, kk = gb % NPH;
+        const int gm = (NMU - 1 - jj) * NPH + kk;   // mirror angle (reflecting wall)
+        const bool up = vn >= T(0);
+        const T taug = S.taus[gb];
+        for (int i = gc; i < NE; i += nch) {
+          const int q = i * NA + gb;
+          T fs;
+          if (F.type == F_INTERNAL) {
+            const T g1 = G1[q], g2 = G2[q];
+            const T flw = RD[q] + S.ksS[i] * S.rowJ[i] * taug * ID[q];
+            T fu, w;
+            if (up) {
+              T sl = T(0);
+              if (F.z[0] >= 0) sl = mc_limiter((g1 - G0[q]) * ft.rdl0, (g2 - g1) * ft.rdl1);
+              fu = g1 + sl * ft.sP;
+              w = S.wP[i];
+            } else {
+              T sl = T(0);
+              if (F.z[3] >= 0) sl = mc_limiter((g2 - g1) * ft.rdl1, (G3[q] - g2) * ft.rdl2);
+              fu = g2 + sl * ft.sQ;
+              w = S.wQ[i];
+            }
+            fs = (T(1) - w) * flw + w * fu;
+          } else if (F.type == F_OUTFLOW_P) {
+            fs = up ? G1[q] : T(0);
+          } else if (F.type == F_OUTFLOW_Q) {
+            fs = vn < T(0) ? G2[q] : T(0);
+          } else {  // reflecting wall at rest
+            fs = vn < T(0) ? G2[q] : G2[i * NA + gm];
           }
-          fs = (T(1) - w) * flw + w * fu;
-        } else if (F.type == F_OUTFLOW_P) {
-          fs = vn >= T(0) ? S.g[nbin + q] : T(0);
-        } else if (F.type == F_OUTFLOW_Q) {
-          fs = vn < T(0) ? S.g[2 * nbin + q] : T(0);
-        } else {  // reflecting wall at rest
-          int j = ang / NPH, k = ang % NPH;
-          int qm = i * NA + (NMU - 1 - j) * NPH + k;
-          fs = vn < T(0) ? S.g[2 * nbin + q] : S.g[2 * nbin + qm];
+          const T Fc = fang * S.dGam[i] * fs;
+          FL[q] = Fc;
+          if (sizeof(T) == 4) sumF = ff_add(sumF, (float)Fc);
+          if (outflow) {
+            double c = (F.type == F_OUTFLOW_P ? 1.0 : -1.0) * (double)Fc;
+            tn += c;
+            te += c * tb.eps[i] * (double)S.u0s[gb];
+          }
         }
-        S.src[q] = (T)dt * (T)F.area * c6s * S.u0s[ang] * vn * (T)tb.dGam[i] * (T)tb.dOm[ang] * fs;
       }
-      __syncthreads();
+      if (sizeof(T) == 4) sumF = block_sum_ff(sumF, S.redf);
+      else __syncthreads();
+      // the stencil buffers are free: prefetch the next rows while depositing
+      {
+        int fn = fidx, sn = s + 1;
+        if (sn == NS) { fn = next_face(fidx); sn = 0; }
+        if (fn < nface) issue(fn, sn);
+      }
+      if (tid == 0 && sizeof(T) == 4) {
+        // exact total of this zone's deposits: (+sum F if own Q) - (sum F if own P)
+        if (F.own & 2) S.dtot[s] = ff_add(S.dtot[s], sumF);
+        if (F.own & 1) S.dtot[s] = ff_add(S.dtot[s], ff_neg(sumF));
+      }
       // outflow tallies (number and energy at infinity)
-      if (F.type == F_OUTFLOW_P || F.type == F_OUTFLOW_Q) {
-        double sg = F.type == F_OUTFLOW_P ? 1.0 : -1.0;
-        double tn = 0.0, te = 0.0;
-        for (int q = tid; q < nbin; q += kThreads) {
-          int i = q / NA, ang = q % NA;
-          double c = sg * (double)S.src[q];
-          tn += c;
-          te += c * F.al * tb.eps[i] * (double)S.u0s[ang];
-        }
+      if (outflow) {
         double te_sum;
         double tn_sum = block_sum2(tn, te, S.red, te_sum);
-        if (tid == 0) { S.tally[2 * s] += tn_sum; S.tally[2 * s + 1] += te_sum; }
+        if (tid == 0) { S.tally[2 * s] += tn_sum; S.tally[2 * s + 1] += te_sum * F.al; }
       }
       // deposits into this zone: dN -= T_{s->P}[F] (own P), dN += T_{s->Q}[F] (own Q)
-      double* dNs = S.dN + (size_t)s * nbin;
-      for (int q = tid; q < nbin; q += kThreads) {
-        int ip = q / NA, bp = q % NA;
-        double acc = 0.0;
-        if (F.own & 1) acc -= gather_bin<T, double>(ip, bp, NE, NA, NMU, NPH, S.src, S.W + 4 * NA, S.off + 4 * (nkeys + 1), S.list + 4 * NA);
-        if (F.own & 2) acc += gather_bin<T, double>(ip, bp, NE, NA, NMU, NPH, S.src, S.W + 5 * NA, S.off + 5 * (nkeys + 1), S.list + 5 * NA);
-        dNs[q] += acc;
+      T* EP = EB + 2 * nbin;
+      T* EQ = EB + 3 * nbin;
+      if (gact) {
+        if (F.own & 1) energy_column<T, T>(gc, nch, NE, NA, gb, em[4], ew[4], FL, EP);
+        if (F.own & 2) energy_column<T, T>(gc, nch, NE, NA, gb, em[5], ew[5], FL, EQ);
+      }
+      __syncthreads();
+      if (gact) {
+        DN* dNs = S.dN + (size_t)s * nbin;
+        const short* offP = S.off + 4 * (NA + 1);
+        const short* offQ = S.off + 5 * (NA + 1);
+        if (F.own & 1)
+          angular_rows<T, T>(gc, nch, NE, NA, offP[gb], offP[gb + 1], S.ent + 4 * 4 * NA, EP, AddDN<T>{dNs, NA, gb, T(-1)});
+        if (F.own & 2)
+          angular_rows<T, T>(gc, nch, NE, NA, offQ[gb], offQ[gb + 1], S.ent + 5 * 4 * NA, EQ, AddDN<T>{dNs, NA, gb, T(1)});
       }
       __syncthreads();
     }
   }
 
+  // --- mixed path: restore the exact deposit total of every species before
+  //     the collision (float accumulation rounds; number must not drift)
+  if (sizeof(T) == 4) {
+    for (int s = 0; s < NS; ++s) {
+      const DN* dNs = S.dN + (size_t)s * nbin;
+      ff part = ff{0.0f, 0.0f};
+      float bk = -1.0f;
+      int bi = 0x7fffffff;
+      for (int q = tid; q < nbin; q += kThreads) {
+        part = ff_add(part, (float)dNs[q]);
+        float k = fabsf((float)dNs[q]);
+        if (k > bk) { bk = k; bi = q; }
+      }
+      ff tot = block_sum_ff(part, S.redf);
+      int at = block_argmax(bk, bi, S.rkey, S.ridx);
+      if (tid == 0) {
+        ff c = ff_add(S.dtot[s], ff_neg(tot));
+        S.corr[s] = ff_to_d(c);
+        S.corr_at[s] = at;
+      }
+    }
+  } else {
+    for (int s = tid; s < NS; s += kThreads) { S.corr[s] = 0.0; S.corr_at[s] = -1; }
+  }
+
   // --- implicit collision per (species, group) (Sec. 3.5) and moments (Eq. hydrosource)
-  const double alz = st.al[zone], c6z = pow(st.cf[zone], 6.0), volz = tb.vol[zone];
+  const double alz = st.al[zone], c6z = pow6(st.cf[zone]), volz = tb.vol[zone];
+  const double rdt = 1.0 / dt;
   {
     const double* v = st.v + 3 * zone;
     double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
@@ -702,7 +1130,10 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
     for (int ang = tid; ang < NA; ang += kThreads) {
       int j = ang / NPH, k = ang % NPH;
       double nv = v[0] * tb.mu[j] + (v[1] * tb.cph[k] + v[2] * tb.sph[k]) * tb.smu[j];
-      S.zu0[ang] = gz * (1.0 + nv);
+      double u0 = gz * (1.0 + nv);
+      S.zu0[ang] = u0;
+      S.ztau[ang] = alz * dt / u0;
+      S.zcn[ang] = 1.0 / (c6z * volz * u0 * tb.dOm[ang]);
     }
   }
   __syncthreads();
@@ -710,18 +1141,25 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
     const int s = row / NE, i = row % NE;
     const size_t oz = ((size_t)s * tb.n_zone + zone) * NE + i;
     const double ka = st.ka[oz], ks = st.ks[oz], fe = st.fe[oz];
+    const double kt = ka + ks, kafe = ka * fe, rdg = 1.0 / tb.dGam[i];
     const T* fz = fin + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
-    const double* dn = S.dN + (size_t)s * nbin + (size_t)i * NA;
-    const double dg = tb.dGam[i];
+    const DN* dn = S.dN + (size_t)s * nbin + (size_t)i * NA;
+    const int cat = S.corr_at[s] - i * NA;       // corrected bin of this row, if any
+    const double cval = S.corr[s];
+    double* rr = S.wr_r + (size_t)warp * NA;
+    double* ri = S.wr_i + (size_t)warp * NA;
     double sr = 0.0, s1 = 0.0;
     for (int ang = lane; ang < NA; ang += 32) {
-      double u0 = S.zu0[ang];
-      double tau = alz * dt / u0;
-      double fst = (double)fz[ang] + dn[ang] / (c6z * volz * u0 * dg * tb.dOm[ang]);
-      double r = fst + tau * ka * fe;
-      double D = 1.0 + (ka + ks) * tau;
-      sr += tb.dOm[ang] * r / D;
-      s1 += tb.dOm[ang] * (1.0 + ka * tau) / D;
+      double tau = S.ztau[ang];
+      double dnv = (double)dn[ang] + (ang == cat ? cval : 0.0);
+      double fst = (double)fz[ang] + dnv * S.zcn[ang] * rdg;
+      double r = fst + tau * kafe;
+      double iD = 1.0 / (1.0 + kt * tau);
+      rr[ang] = fst;
+      ri[ang] = iD;
+      double dom = tb.dOm[ang];
+      sr += dom * r * iD;
+      s1 += dom * (1.0 + ka * tau) * iD;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -732,24 +1170,23 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
     double mN = 0.0, mE = 0.0, mP0 = 0.0, mP1 = 0.0, mP2 = 0.0;
     int bad = 0;
     T* fo = fout + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
+    const double cdg = c6z * tb.dGam[i] * rdt;
     for (int ang = lane; ang < NA; ang += 32) {
-      const int j = ang / NPH, k = ang % NPH;
-      double u0 = S.zu0[ang];
-      double tau = alz * dt / u0;
-      double fst = (double)fz[ang] + dn[ang] / (c6z * volz * u0 * dg * tb.dOm[ang]);
-      double r = fst + tau * ka * fe;
-      double D = 1.0 + (ka + ks) * tau;
-      double fn = (r + ks * tau * J) / D;
+      double tau = S.ztau[ang];
+      double fst = rr[ang];
+      double r = fst + tau * kafe;
+      double fn = (r + ks * tau * J) * ri[ang];
       T fw = (T)fn;
       fo[ang] = fw;
       bad |= !isfinite(fn);
-      double dc = c6z * u0 * dg * tb.dOm[ang] * ((double)fw - fst) / dt;
-      mN += dc;
-      double de = dc * tb.eps[i];
-      mE += de;
-      mP0 += de * tb.mu[j];
-      mP1 += de * tb.smu[j] * tb.cph[k];
-      mP2 += de * tb.smu[j] * tb.sph[k];
+      // collision moments in the arithmetic type (float64 path: float64)
+      T dc = (T)(cdg * S.zu0[ang] * tb.dOm[ang] * ((double)fw - fst));
+      mN += (double)dc;
+      T de = dc * (T)tb.eps[i];
+      mE += (double)de;
+      mP0 += (double)(de * S.n0[ang]);
+      mP1 += (double)(de * S.n1[ang]);
+      mP2 += (double)(de * S.n2[ang]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -797,13 +1234,14 @@ __global__ void __launch_bounds__(kThreads) k_flux_collide(Tables tb, State st, 
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RemapSmem {
-  T* src; T* mu; Wt<T>* W; short* off; short* list; int* cnt;
+  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam;
+  Wt<T>* W; AEnt<T>* ent; short* off; int* cnt;
+  ff* redf; float* rkey; int* ridx;
 };
 
 template <typename T>
-__host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, int nph, RemapSmem<T>* s, unsigned char* base) {
+__host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSmem<T>* s, unsigned char* base) {
   size_t o = 0;
-  const int nkeys = (nmu >= 2 ? nmu - 1 : 1) * nph;
 #define BT_TAKE(ptr, type, count)                              \
   do {                                                         \
     o = (o + 15) & ~size_t(15);                                \
@@ -811,11 +1249,21 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, int nph,
     o += sizeof(type) * (size_t)(count);                       \
   } while (0)
   BT_TAKE(src, T, (size_t)ne * nang);
+  BT_TAKE(E, T, (size_t)ne * nang);
+  BT_TAKE(dst, T, (size_t)ne * nang);
   BT_TAKE(mu, T, nmu);
+  BT_TAKE(n0, T, nang);
+  BT_TAKE(n1, T, nang);
+  BT_TAKE(n2, T, nang);
+  BT_TAKE(dOm, T, nang);
+  BT_TAKE(dGam, T, ne);
   BT_TAKE(W, Wt<T>, nang);
-  BT_TAKE(off, short, nkeys + 1);
-  BT_TAKE(list, short, nang);
-  BT_TAKE(cnt, int, nkeys);
+  BT_TAKE(ent, AEnt<T>, 4 * nang);
+  BT_TAKE(off, short, nang + 1);
+  BT_TAKE(cnt, int, nang);
+  BT_TAKE(redf, ff, kWarps);
+  BT_TAKE(rkey, float, kWarps);
+  BT_TAKE(ridx, int, kWarps);
 #undef BT_TAKE
   return (o + 15) & ~size_t(15);
 }
@@ -824,38 +1272,66 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RemapSmem<T> S;
-  remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, &S, smem_raw);
+  remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, &S, smem_raw);
   const int zone = blockIdx.x;
   const int NE = tb.n_e, NA = tb.n_ang, NPH = tb.n_ph, NMU = tb.n_mu;
-  const int nbin = NE * NA, nkeys = nkeys_of(tb);
+  const int nbin = NE * NA;
   const int tid = threadIdx.x;
+  const int nch = kThreads / NA > 0 ? kThreads / NA : 1;
+  const int gb = tid % NA, gc = tid / NA;
+  const bool gact = tid < nch * NA;
   for (int q = tid; q < NMU; q += kThreads) S.mu[q] = (T)tb.mu[q];
+  for (int q = tid; q < NA; q += kThreads) {
+    int j = q / NPH, k = q % NPH;
+    S.n0[q] = (T)tb.mu[j];
+    S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
+    S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
+    S.dOm[q] = (T)tb.dOm[q];
+  }
+  for (int q = tid; q < NE; q += kThreads) S.dGam[q] = (T)tb.dGam[q];
   __syncthreads();
   Loc<T> X, Y;
   make_loc(X, st.v_old + 3 * zone, st.al_old[zone], st.cf_old[zone]);
   make_loc(Y, st.v + 3 * zone, st.al[zone], st.cf[zone]);
   for (int ang = tid; ang < NA; ang += kThreads) chain_weights(tb, S.mu, X, Y, nullptr, 0, AX_TIME, ang, S.W[ang]);
   __syncthreads();
-  if (tid < 32) build_buckets(S.W, NA, NPH, nkeys, S.off, S.list, S.cnt);
-  __syncthreads();
-  const T c6x = (T)pow(st.cf_old[zone], 6.0), c6y = (T)pow(st.cf[zone], 6.0);
+  const int em = gact ? S.W[gb].m : 0;
+  const T ew = gact ? S.W[gb].we : T(0);
+  build_alists(S.W, 1, 1u, NA, NMU, NPH, S.off, S.cnt, S.ent);
+  const T c6x = (T)pow6(st.cf_old[zone]), c6y = (T)pow6(st.cf[zone]);
   T* f = reinterpret_cast<T*>(st.f);
   for (int s = 0; s < tb.n_s; ++s) {
     T* fz = f + ((size_t)s * tb.n_zone + zone) * nbin;
-    for (int q = tid; q < nbin; q += kThreads) {
-      int i = q / NA, ang = q % NA;
-      int j = ang / NPH, k = ang % NPH;
-      T nv = X.v[0] * S.mu[j] + (X.v[1] * (T)tb.cph[k] + X.v[2] * (T)tb.sph[k]) * (T)tb.smu[j];
-      S.src[q] = c6x * X.g * (T(1) + nv) * (T)tb.dGam[i] * (T)tb.dOm[ang] * fz[q];
+    ff part = ff{0.0f, 0.0f};
+    if (gact) {
+      const T u0 = X.g * (T(1) + (X.v[0] * S.n0[gb] + X.v[1] * S.n1[gb] + X.v[2] * S.n2[gb]));
+      const T cang = c6x * u0 * S.dOm[gb];
+      for (int i = gc; i < NE; i += nch) {
+        const int q = i * NA + gb;
+        T d = cang * S.dGam[i] * fz[q];
+        S.src[q] = d;
+        if (sizeof(T) == 4) part = ff_add(part, (float)d);
+      }
     }
+    ff tot_in = ff{0.0f, 0.0f};
+    if (sizeof(T) == 4) tot_in = block_sum_ff(part, S.redf);
+    else __syncthreads();
+    if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, S.src, S.E);
     __syncthreads();
-    for (int q = tid; q < nbin; q += kThreads) {
-      int ip = q / NA, bp = q % NA;
-      int j = bp / NPH, k = bp % NPH;
-      double d = gather_bin<T, double>(ip, bp, NE, NA, NMU, NPH, S.src, S.W, S.off, S.list);
-      T nv = Y.v[0] * S.mu[j] + (Y.v[1] * (T)tb.cph[k] + Y.v[2] * (T)tb.sph[k]) * (T)tb.smu[j];
-      T u0 = Y.g * (T(1) + nv);
-      fz[q] = (T)(d / ((double)c6y * (double)u0 * tb.dGam[ip] * tb.dOm[bp]));
+    if (gact) angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
+    __syncthreads();
+    int at = -1;
+    ff corr = ff{0.0f, 0.0f};
+    if (sizeof(T) == 4) corr = conservation_residual(S.dst, nbin, tot_in, S.redf, S.rkey, S.ridx, &at);
+    if (gact) {
+      const T u0 = Y.g * (T(1) + (Y.v[0] * S.n0[gb] + Y.v[1] * S.n1[gb] + Y.v[2] * S.n2[gb]));
+      const T cang = c6y * u0 * S.dOm[gb];
+      for (int ip = gc; ip < NE; ip += nch) {
+        const int q = ip * NA + gb;
+        T d = S.dst[q];
+        if (q == at) d = (T)((double)d + ff_to_d(corr));
+        fz[q] = d / (cang * S.dGam[ip]);
+      }
     }
     __syncthreads();
   }
@@ -874,7 +1350,7 @@ __global__ void __launch_bounds__(kThreads) k_zone_totals(Tables tb, State st) {
   const T* f = reinterpret_cast<const T*>(st.f);
   const double* v = st.v + 3 * zone;
   const double gz = 1.0 / sqrt(1.0 - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
-  const double c6 = pow(st.cf[zone], 6.0), al = st.al[zone], vol = tb.vol[zone];
+  const double c6 = pow6(st.cf[zone]), al = st.al[zone], vol = tb.vol[zone];
   for (int s = 0; s < tb.n_s; ++s) {
     const T* fz = f + ((size_t)s * tb.n_zone + zone) * nbin;
     double sn = 0.0, se = 0.0;
@@ -1004,7 +1480,7 @@ __global__ void k_jhk(Tables tb, State st, double* J, double* H, double* K) {
 
 template <typename T>
 int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) {
-  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, nullptr, nullptr);
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
   cudaError_t e = cudaFuncSetAttribute(k_flux_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return (int)e;
   k_flux_collide<T><<<tb.n_zone, kThreads, sm, s>>>(tb, st, dt);
@@ -1013,7 +1489,7 @@ int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) 
 
 template <typename T>
 int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
-  size_t sm = remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, nullptr, nullptr);
+  size_t sm = remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
   cudaError_t e = cudaFuncSetAttribute(k_time_remap<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return (int)e;
   k_time_remap<T><<<tb.n_zone, kThreads, sm, s>>>(tb, st);
@@ -1023,12 +1499,12 @@ int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
 }  // namespace
 
 size_t flux_smem_bytes(const Tables& tb, int mixed) {
-  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, nullptr, nullptr)
-               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, nullptr, nullptr);
+  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr)
+               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
 }
 size_t remap_smem_bytes(const Tables& tb, int mixed) {
-  return mixed ? remap_smem_layout<float>(tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, nullptr, nullptr)
-               : remap_smem_layout<double>(tb.n_e, tb.n_ang, tb.n_mu, tb.n_ph, nullptr, nullptr);
+  return mixed ? remap_smem_layout<float>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr)
+               : remap_smem_layout<double>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
 }
 int max_optin_smem() {
   int dev = 0, v = 0;
