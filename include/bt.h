@@ -171,6 +171,30 @@ enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2 };
 int bt_profile(bt_handle* h, int enable);
 int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launches);
 
+/* Weighted totals of a distribution without any device allocation.
+ * The paper has no counterpart: this is a library service for callers that
+ * cannot allocate device memory -- e.g. a host code whose own allocator owns
+ * all device memory, or a loop that must never allocate.
+ *   out[s] = sum over zone z, group i, angle b of
+ *            w_za[z][b] * w_e[i] * f[s][z][i][b]
+ * (with w_za = dV phi^6 u^0 dOmega and w_e = dGamma this is the number of
+ * species s that bt_totals reports).  All pointers are DEVICE pointers owned
+ * by the caller; f is float64 (precision BT_FP64) or float32 (BT_MIXED) in the
+ * layout above; out receives n_s doubles.  Work is enqueued on `stream`
+ * (cudaStream_t); the call does not synchronise.
+ * Scratch: per-block partial sums live in one file-scope device array of
+ * 2 * BT_NOALLOC_MAX_PARTIALS doubles (1 MiB) that every GPU loading the
+ * library holds until the process exits; n_s * ceil(n_zone / 64) must not
+ * exceed BT_NOALLOC_MAX_PARTIALS (else BT_ERR_ARG).  The first call on a
+ * device looks up that array's device address (with that device current),
+ * so make it before any stream capture.  Every call overwrites the partials it
+ * reads, so nothing needs clearing, but calls that overlap on the GPU race on
+ * the shared array.  Returns BT_OK, BT_ERR_ARG or BT_ERR_CUDA; bt_last_error()
+ * is not updated by this call.  It calls no cudaMalloc/cudaFree. */
+#define BT_NOALLOC_MAX_PARTIALS (1 << 16)
+int bt_weighted_totals_noalloc(const void* f, int precision, int n_s, int n_zone, int n_e, int n_ang,
+                               const double* w_za, const double* w_e, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

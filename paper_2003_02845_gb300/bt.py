@@ -64,6 +64,7 @@ def lib():
         L.bt_jhk.argtypes = [vp, i32, dp, dp, dp]
         L.bt_launch_count.restype = C.c_int64
         L.bt_launch_count.argtypes = [vp]
+        L.bt_weighted_totals_noalloc.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp, vp, vp]
         L.bt_profile.argtypes = [vp, i32]
         L.bt_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         _lib = L
@@ -219,6 +220,21 @@ class Transport:
 
 
 K_TIME_REMAP, K_FLUX, K_OUTFLOW = 0, 1, 2
+
+
+def weighted_totals_noalloc(f, w_za, w_e, precision: str, out, stream=None):
+    """Allocation-free weighted totals (see bt_weighted_totals_noalloc in
+    include/bt.h).  f, w_za, w_e, out: contiguous CUDA tensors (f float64 or
+    float32 as `precision` says, weights and out float64)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    n_s, n_zone, n_e, n_ang = f.shape
+    rc = lib().bt_weighted_totals_noalloc(f.data_ptr(), BT_MIXED if precision == "mixed" else BT_FP64,
+                                          n_s, n_zone, n_e, n_ang, w_za.data_ptr(), w_e.data_ptr(),
+                                          out.data_ptr(), s.cuda_stream)
+    if rc != BT_OK:
+        raise BtError(rc, "bt_weighted_totals_noalloc failed")
+    return out
 
 
 def run(prob, precision="fp64", n_steps=None, dt=None, cfl=None):
