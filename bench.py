@@ -116,6 +116,27 @@ def dist_init(n_gpus):
     return rank, world
 
 
+# GB300 unit counts and clock (nominal): 152 SMs, 128 FP32 lanes per SM,
+# float64 at 1/64 of the float32 rate, maximum SM clock 2070 MHz.  A fused
+# multiply-add counts as two flops.
+GB300_SMS, GB300_FP32_LANES, GB300_SM_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = GB300_SMS * GB300_FP32_LANES * 2 * GB300_SM_GHZ / 1e3
+FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
+
+
+def algorithmic_flops_per_bin(prob):
+    """Arithmetic the method needs per zone-group-angle-species bin and step,
+    counted on unique faces (3 per zone in spherical geometry, 1 in a slab):
+    per face six remaps (four stencil cells into the face frame, the flux
+    back into both neighbours), each a trilinear split costing 6 FMA per bin;
+    about 28 flops for the Lax-Wendroff half step, MC upwind, blend and flux;
+    the weight chain (~150 flops per remap and angle) shared by all groups and
+    species; and ~20 flops for the implicit collision."""
+    faces = 1 if prob.geom == 1 else 3
+    per_face = 6 * 12 + 28 + 6 * 150.0 / (prob.n_eps * prob.n_species)
+    return faces * per_face + 20.0
+
+
 def algorithmic_bytes_per_bin(prob, mixed):
     """Bytes that one full step must move per zone-group-angle-species bin:
     read f^n and write f^{n+1}, plus the opacities (3 float64 per zone, group
@@ -213,8 +234,11 @@ def run_ours(args):
 
     peaks, peak_src = load_peaks()
     bpb = algorithmic_bytes_per_bin(prob, mixed)
+    fpb = algorithmic_flops_per_bin(prob)
     flux_avg_ms = flux_ms / max(flux_n, 1)
-    achieved = bins * bpb / (flux_avg_ms * 1e-3) / 1e9
+    achieved_gbs = bins * bpb / (flux_avg_ms * 1e-3) / 1e9
+    achieved_tf = bins * fpb / (flux_avg_ms * 1e-3) / 1e12
+    peak_tf = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
     peak = hbm_peak(peaks)
     res = {
         "metric": METRIC,
@@ -244,17 +268,20 @@ def run_ours(args):
         "e2e": {"value": world * units_per_step / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {
-            "kernel": "k_flux_collide",
-            "bound": "hbm",
-            "achieved": achieved,
-            "peak": peak,
-            "peak_source": peak_src,
-            "unit": "GB/s",
-            "frac": achieved / peak,
+            "kernel": "k_flux_collide<%s>" % ("float" if mixed else "double"),
+            "bound": "alu",
+            "achieved": achieved_tf,
+            "peak": peak_tf,
+            "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.2f GHz%s" % (
+                GB300_SMS, GB300_FP32_LANES, GB300_SM_GHZ, "" if mixed else " / 64 (float64)"),
+            "unit": "TFLOP/s",
+            "frac": achieved_tf / peak_tf,
             "traffic": None,
-            "algorithmic_bytes_per_bin": bpb,
+            "algorithmic_flops_per_bin": fpb,
             "avg_launch_ms": flux_avg_ms,
             "time_remap_avg_ms": remap_ms / max(remap_n, 1),
+            "hbm": {"achieved": achieved_gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                    "frac": achieved_gbs / peak, "algorithmic_bytes_per_bin": bpb},
         },
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -172,7 +172,7 @@ int plan(const bt_config* c, WsPlan& P, size_t* tab_sizes) {
       (size_t)c->n_mu, (size_t)c->n_mu, (size_t)c->n_phi, (size_t)c->n_phi, nang, ne, ne, nz,
       (size_t)c->n_r + 1, (size_t)c->n_r, nth + 1, nth,
       nth * (c->n_r + 1), (nth + 1) * c->n_r, nth * c->n_r,
-      nth * 9, (nth + 1) * 4 * 9, nth * 4 * 9};
+      nth * 9, (nth + 1) * 4 * 9, nth * 4 * 9, 2 * ne + 3};
   const int ntab = sizeof(sizes) / sizeof(sizes[0]);
   for (int i = 0; i < ntab; ++i) {
     tab_sizes[i] = sizes[i];
@@ -351,8 +351,11 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
       }
     }
   }
+  // ratios dGamma_i / dGamma_t = R^(3 (i - t)) of the log-uniform group grid
+  std::vector<double> p3(2 * ne + 3);
+  for (int k = -(ne + 1); k <= ne + 1; ++k) p3[k + ne + 1] = std::pow(R, 3.0 * k);
   const std::vector<double>* tabs[] = {&mu, &smu, &cph, &sph, &dOm, &dGam, &eps, &vol, &r_e, &r_c,
-                                       &th_e, &th_c, &ar, &at, &ap, &Gr, &Gt, &Gp};
+                                       &th_e, &th_c, &ar, &at, &ap, &Gr, &Gt, &Gp, &p3};
   for (int i = 0; i < ntab; ++i) {
     cudaError_t e = cudaMemcpyAsync(base + P.tables[i], tabs[i]->data(), 8 * ts[i], cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) { bt_destroy(h); return cuda_fail(e, "upload tables"); }
@@ -370,6 +373,7 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   T.r_e = D(P.tables[8]); T.r_c = D(P.tables[9]); T.th_e = D(P.tables[10]); T.th_c = D(P.tables[11]);
   T.area_r = D(P.tables[12]); T.area_t = D(P.tables[13]); T.area_p = D(P.tables[14]);
   T.G_r = D(P.tables[15]); T.G_t = D(P.tables[16]); T.G_p = D(P.tables[17]);
+  T.p3 = D(P.tables[18]);
   T.species_kind = reinterpret_cast<const int*>(base + P.tables[ntab]);
 
   for (int s = 0; s < 2; ++s)

@@ -29,6 +29,7 @@ struct Tables {
   const double* dOm;   // [n_ang]
   const double* dGam;  // [n_e]
   const double* eps;   // [n_e] group centres
+  const double* p3;    // [2 n_e + 3] R^(3k) for k = -(n_e+1) .. n_e+1 (dGamma ratios)
   const double* vol;   // [n_zone]
   const double* r_e;   // [n_r + 1]
   const double* r_c;   // [n_r]

@@ -138,14 +138,10 @@ __device__ __forceinline__ float exp_t(float x) { return expf(x); }
 // -> rotation G (src triad -> dst triad; transposed if gT) -> comoving(dst),
 // then the trilinear weights (Sec. 3.2, Eq. interpolation).
 template <typename T>
-__device__ void chain_weights(const Tables& tb, const T* s_mu, const Loc<T>& X, const Loc<T>& Y,
-                              const double* G, int gT, int axis, int ang, Wt<T>& w) {
-  const int j = ang / tb.n_ph, k = ang % tb.n_ph;
-  T n[3];
-  n[0] = s_mu[j];
-  T sm = (T)tb.smu[j];
-  n[1] = sm * (T)tb.cph[k];
-  n[2] = sm * (T)tb.sph[k];
+__device__ void chain_weights(const Tables& tb, const T* s_mu, const T* n0, const T* n1, const T* n2,
+                              const Loc<T>& X, const Loc<T>& Y, const T* G, int gT, int axis, int ang, T R,
+                              Wt<T>& w) {
+  T n[3] = {n0[ang], n1[ang], n2[ang]};
   T e, p[3];
   boost_fwd(X, n, e, p);
   T a = X.al / Y.al;
@@ -155,8 +151,8 @@ __device__ void chain_weights(const Tables& tb, const T* s_mu, const Loc<T>& X, 
     T q[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m)
-      q[m] = gT ? ((T)G[m] * p[0] + (T)G[3 + m] * p[1] + (T)G[6 + m] * p[2])
-                : ((T)G[3 * m] * p[0] + (T)G[3 * m + 1] * p[1] + (T)G[3 * m + 2] * p[2]);
+      q[m] = gT ? (G[m] * p[0] + G[3 + m] * p[1] + G[6 + m] * p[2])
+                : (G[3 * m] * p[0] + G[3 * m + 1] * p[1] + G[3 * m + 2] * p[2]);
     p[0] = q[0]; p[1] = q[1]; p[2] = q[2];
   }
   boost_inv(Y, e, p);
@@ -166,7 +162,6 @@ __device__ void chain_weights(const Tables& tb, const T* s_mu, const Loc<T>& X, 
   T phs = atan2_t(p[2], p[1]);
   if (phs < T(0)) phs += T(2 * kPi);
   // energy: eps* = rho eps_i, bracket eps_{i+m} <= eps* < eps_{i+m+1}
-  T R = (T)tb.R;
   int m = (int)floor_t(log_t(rho) / log_t(R));
   T t = rho / pow_t(R, (T)m);
   T we = (t - T(1)) / (R - T(1));
@@ -191,7 +186,7 @@ __device__ void chain_weights(const Tables& tb, const T* s_mu, const Loc<T>& X, 
   if (nph == 1) {
     kL = 0; wp = T(0);
   } else {
-    T u = phs / T(2 * kPi / nph) - T(0.5);
+    T u = phs * (T(nph) * T(1.0 / (2 * kPi))) - T(0.5);
     T kf = floor_t(u);
     wp = u - kf;
     kL = ((int)kf) % nph;
@@ -231,6 +226,38 @@ __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ ff ff_shfl_down(ff a, int o) {
   return ff{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ ff ff_shfl_xor(ff a, int o) {
+  return ff{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+// |a| >= |b| (Dekker's Fast2Sum)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  float s = a + b;
+  return ff{s, b - (s - a)};
+}
+// error-free product with a fused multiply-add
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  float p = a * b;
+  return ff{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.hi, b.hi);
+  float lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, lo);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  ff p = two_prod(a.hi, b);
+  return fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+// 1/d by one Newton step from the float reciprocal: x + x (1 - d x)
+__device__ __forceinline__ ff ff_recip(ff d) {
+  float x = 1.0f / d.hi;
+  ff e = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul_f(d, x)));
+  return ff_add(ff{x, 0.0f}, ff_mul_f(e, x));
+}
+__device__ __forceinline__ ff ff_from_d(double v) {
+  float hi = (float)v;
+  return ff{hi, (float)(v - (double)hi)};
 }
 
 // ---------------------------------------------------------------------------
@@ -304,6 +331,7 @@ __device__ __forceinline__ int ang_targets(const Wt<T>& W, int nmu, int nph, int
       int kt = dk ? kR : kL;
       int t = jt * nph + kt;
       T w = mj[dj] * mk[dk];
+      if (w == T(0)) continue;        // adds nothing: keep the lists short
       int q = 0;
       while (q < n && tgt[q] != t) ++q;
       if (q == n) { tgt[n] = t; wa[n] = w; ++n; }
@@ -385,30 +413,33 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
   __syncthreads();
 }
 
-// Energy pass for column b (source angle b, shift m, upper weight we):
-// E[t] = sum over source groups i with clamp(i+m) == t of (1-we) c_i src[i]
-//      + sum over i with clamp(i+m+1) == t of we c_i src[i],
-// with c_i = cang * rowf[i] (rowf == nullptr: c_i = 1), which folds the
-// conversion of f into content density into the pass.
+// Energy pass for column b (source angle b, shift m, upper weight we) in
+// "y-form" (content per unit dGamma): source group i goes to groups
+// clamp(i+m) (weight 1-we) and clamp(i+m+1) (we), and its content per unit
+// dGamma is rescaled by dGamma_i / dGamma_t = R^(3(i-t)) (p3c[k] = R^(3k)):
+//   E[t] = c * sum_i w(t|i) R^(3(i-t)) src[i].
 template <typename T, typename A>
 __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, int b, int m, T we, const T* src, T* E,
-                                              T cang = T(1), const T* rowf = nullptr) {
-  const A wl = (A)cang * (A(1) - (A)we), wr = (A)cang * (A)we;
+                                              T c, const T* p3c) {
+  const A wl = (A)c * (A(1) - (A)we), wr = (A)c * (A)we;
+  const bool small = m > -ne && m < ne;   // interior sources exist only then
+  const A wli = small ? wl * (A)p3c[-m] : A(0);
+  const A wri = (m >= -ne && m < ne - 1) ? wr * (A)p3c[-m - 1] : A(0);
   for (int t = gc; t < ne; t += nch) {
     A acc = A(0);
     if (t > 0 && t < ne - 1) {
       int iL = t - m, iR = t - m - 1;
-      if (iL >= 0 && iL < ne) acc += wl * (rowf ? (A)rowf[iL] : A(1)) * (A)src[iL * na + b];
-      if (iR >= 0 && iR < ne) acc += wr * (rowf ? (A)rowf[iR] : A(1)) * (A)src[iR * na + b];
+      if (iL >= 0 && iL < ne) acc += wli * (A)src[iL * na + b];
+      if (iR >= 0 && iR < ne) acc += wri * (A)src[iR * na + b];
     } else {
       int lo = (t == 0) ? 0 : t - m;
       int hi = (t == ne - 1) ? ne - 1 : t - m;
       lo = max(lo, 0); hi = min(hi, ne - 1);
-      for (int i = lo; i <= hi; ++i) acc += wl * (rowf ? (A)rowf[i] : A(1)) * (A)src[i * na + b];
+      for (int i = lo; i <= hi; ++i) acc += wl * (A)p3c[i - t] * (A)src[i * na + b];
       lo = (t == 0) ? 0 : t - m - 1;
       hi = (t == ne - 1) ? ne - 1 : t - m - 1;
       lo = max(lo, 0); hi = min(hi, ne - 1);
-      for (int i = lo; i <= hi; ++i) acc += wr * (rowf ? (A)rowf[i] : A(1)) * (A)src[i * na + b];
+      for (int i = lo; i <= hi; ++i) acc += wr * (A)p3c[i - t] * (A)src[i * na + b];
     }
     E[t * na + b] = (T)acc;
   }
@@ -421,7 +452,23 @@ template <typename T, typename A, typename Out>
 __device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int e0, int e1, const AEnt<T>* ent,
                                              const T* E, Out out) {
   const int n = e1 - e0;
-  if (n <= 8) {
+  if (n <= 4) {
+    T w[4];
+    int bb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k < n) { w[k] = ent[e0 + k].w; bb[k] = ent[e0 + k].b; }
+      else { w[k] = T(0); bb[k] = 0; }
+    }
+    for (int t = gc; t < ne; t += nch) {
+      const T* Er = E + t * na;
+      A acc = A(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < n) acc += (A)w[k] * (A)Er[bb[k]];
+      out(t, acc);
+    }
+  } else if (n <= 8) {
     T w[8];
     int bb[8];
 #pragma unroll
@@ -571,6 +618,10 @@ struct FluxSmem {
   double* zu0;     // [nang] own zone u^0
   double* ztau;    // [nang] alpha dt / u^0
   double* zcn;     // [nang] 1/(phi^6 dV u^0 dOmega)
+  ff* zt_f;        // [nang] double-float copies of tau, zcn, dOmega (mixed collision)
+  ff* zc_f;
+  ff* zd_f;
+  float* zq_f;     // [nang] phi^6 u^0 dOmega / dt
   double* zrow;    // [ns][ne][5] collision moment partials
   double* wr_r;    // [kWarps][nang] f* of the warp's collision row   (aliases buf)
   double* wr_i;    // [kWarps][nang] 1/D per warp row                 (aliases buf)
@@ -602,6 +653,9 @@ struct FluxSmem {
   T* kaS; T* ksS; T* feS; T* wP; T* wQ;  // [ne]
   FaceDesc* F;     // [kFaces]
   FaceT<T>* FT;    // [kFaces]
+  Loc<T>* L;       // [kFaces][5] boosts of the stencil cells (0..3) and the face (4)
+  T* Gs;           // [kFaces][4][9] rotations stencil cell -> face in T
+  T* p3;           // [2 ne + 3] R^(3k)
 };
 
 template <typename T>
@@ -619,6 +673,10 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, F
   BT_TAKE(zu0, double, nang);
   BT_TAKE(ztau, double, nang);
   BT_TAKE(zcn, double, nang);
+  BT_TAKE(zt_f, ff, nang);
+  BT_TAKE(zc_f, ff, nang);
+  BT_TAKE(zd_f, ff, nang);
+  BT_TAKE(zq_f, float, nang);
   BT_TAKE(zrow, double, (size_t)ns * ne * 5);
   BT_TAKE(red, double, kWarps * 2);
   BT_TAKE(tally, double, ns * 2);
@@ -672,6 +730,9 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, F
   BT_TAKE(wQ, T, ne);
   BT_TAKE(F, FaceDesc, kFaces);
   BT_TAKE(FT, FaceT<T>, kFaces);
+  BT_TAKE(L, Loc<T>, kFaces * 5);
+  BT_TAKE(Gs, T, kFaces * 36);
+  BT_TAKE(p3, T, 2 * ne + 3);
 #undef BT_TAKE
   return (o + 15) & ~size_t(15);
 }
@@ -758,9 +819,9 @@ __device__ __forceinline__ ff conservation_residual(const double*, int, ff, ff*,
 }
 
 template <typename T>
-struct StoreG {   // g = D / (phi_s^6 u0_s dGamma dOmega) in the face frame
-  T* dst; const T* rdGam; T cs; int na, b;
-  __device__ void operator()(int t, T acc) const { dst[t * na + b] = acc * rdGam[t] * cs; }
+struct StoreG {   // g = D / (phi_s^6 u0_s dOmega) in the face frame (D per unit dGamma)
+  T* dst; T cs; int na, b;
+  __device__ void operator()(int t, T acc) const { dst[t * na + b] = acc * cs; }
 };
 template <typename T>
 struct StoreT {
@@ -810,6 +871,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     S.dOm[q] = (T)tb.dOm[q];
   }
   for (int q = tid; q < NE; q += kThreads) { S.dGam[q] = (T)tb.dGam[q]; S.rdGam[q] = (T)(1.0 / tb.dGam[q]); }
+  for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = (T)tb.p3[q];
   for (int q = tid; q < NS * 2; q += kThreads) S.tally[q] = 0.0;
   for (int q = tid; q < NS; q += kThreads) S.dtot[q] = ff{0.0f, 0.0f};
   if (tid == 0) mbar_init(S.bar, 1);
@@ -828,9 +890,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
       ft.rdl1 = (T)(1.0 / (Fd.x[2] - Fd.x[1]));
       ft.rdl2 = Fd.z[3] >= 0 ? (T)(1.0 / (Fd.x[3] - Fd.x[2])) : T(0);
       for (int k = 0; k < 4; ++k) ft.c6k[k] = Fd.z[k] >= 0 ? (T)pow6(st.cf[Fd.z[k]]) : T(0);
+      // boosts of the stencil cells and the face, rotations in T
+      Loc<T>* L = S.L + 5 * tid;
+      for (int k = 0; k < 4; ++k)
+        if (Fd.z[k] >= 0) make_loc(L[k], st.v + 3 * Fd.z[k], st.al[Fd.z[k]], st.cf[Fd.z[k]]);
+      make_loc(L[4], Fd.v, Fd.al, Fd.cf);
+      T* G = S.Gs + 36 * tid;
+      for (int k = 0; k < 4; ++k)
+        for (int q = 0; q < 9; ++q) G[9 * k + q] = Fd.G[k] ? (T)Fd.G[k][q] : T(q % 4 == 0 ? 1 : 0);
     }
   }
   __syncthreads();
+  const T* P3 = S.p3 + NE + 1;       // P3[k] = R^(3k)
 
   // stencil rows of (face fi, species si) into SRC: bulk copies by thread 0
   auto issue = [&](int fi, int si) {
@@ -861,19 +932,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     if (F.own & 2) mask |= 1u << 5;
 
     // --- weights of the six remaps: slots 0..3 -> face, face -> slot 1, face -> slot 2
+    const Loc<T>* LF = S.L + 5 * fidx;
+    const T* GF = S.Gs + 36 * fidx;
+    const T Rg = (T)tb.R;
     {
-      Loc<T> Ls;
-      make_loc(Ls, F.v, F.al, F.cf);
+      const Loc<T> Ls = LF[4];
       for (int q = tid; q < 6 * NA; q += kThreads) {
         int r = q / NA, ang = q % NA;
         if (!((mask >> r) & 1u)) continue;
         int slot = r < 4 ? r : r - 3;
-        int zz = F.z[slot];
-        Loc<T> Lc;
-        make_loc(Lc, st.v + 3 * zz, st.al[zz], st.cf[zz]);
+        const T* G = F.G[slot] ? GF + 9 * slot : nullptr;
         Wt<T> w;
-        if (r < 4) chain_weights(tb, S.mu, Lc, Ls, F.G[slot], 0, F.axis, ang, w);
-        else chain_weights(tb, S.mu, Ls, Lc, F.G[slot], 1, F.axis, ang, w);
+        if (r < 4) chain_weights(tb, S.mu, S.n0, S.n1, S.n2, LF[slot], Ls, G, 0, F.axis, ang, Rg, w);
+        else chain_weights(tb, S.mu, S.n0, S.n1, S.n2, Ls, LF[slot], G, 1, F.axis, ang, Rg, w);
         S.W[r * NA + ang] = w;
       }
       // face bins: Eulerian energy factor and normal coordinate velocity
@@ -903,10 +974,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     for (int k = 0; k < 4; ++k) {
       cang[k] = T(0);
       if (gact && F.z[k] >= 0) {
-        const double* v = st.v + 3 * F.z[k];
-        const T vx = (T)v[0], vy = (T)v[1], vz = (T)v[2];
-        const T g = T(1) / sqrt(T(1) - (vx * vx + vy * vy + vz * vz));
-        const T u0 = g * (T(1) + (vx * S.n0[gb] + vy * S.n1[gb] + vz * S.n2[gb]));
+        const Loc<T>& Lk = LF[k];
+        const T u0 = Lk.g * (T(1) + (Lk.v[0] * S.n0[gb] + Lk.v[1] * S.n1[gb] + Lk.v[2] * S.n2[gb]));
         cang[k] = ft.c6k[k] * u0 * S.dOm[gb];
       }
     }
@@ -953,7 +1022,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
         for (int slot = 0; slot < 4; ++slot)
           if (F.z[slot] >= 0)
             energy_column<T, T>(gc, nch, NE, NA, gb, em[slot], ew[slot], SRC + slot * nbin, EB + slot * nbin,
-                                cang[slot], S.dGam);
+                                cang[slot], P3);
       }
       __syncthreads();
       // angular pass: g_k = T_{k->s}[n_k] as face distribution (into SRC)
@@ -962,7 +1031,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
         for (int slot = 0; slot < 4; ++slot) {
           if (F.z[slot] < 0) continue;
           const short* off = S.off + slot * (NA + 1);
-          StoreG<T> st_g{SRC + slot * nbin, S.rdGam, csb, NA, gb};
+          StoreG<T> st_g{SRC + slot * nbin, csb, NA, gb};
           angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
         }
       }
@@ -1045,11 +1114,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
           } else {  // reflecting wall at rest
             fs = vn < T(0) ? G2[q] : G2[i * NA + gm];
           }
-          const T Fc = fang * S.dGam[i] * fs;
+          const T Fc = fang * fs;            // flux content per unit dGamma
           FL[q] = Fc;
-          if (sizeof(T) == 4) sumF = ff_add(sumF, (float)Fc);
-          if (outflow) {
-            double c = (F.type == F_OUTFLOW_P ? 1.0 : -1.0) * (double)Fc;
+          if (sizeof(T) == 4) sumF = ff_add(sumF, two_prod((float)Fc, (float)S.dGam[i]));
+        }
+        if (outflow) {
+          const double sg = F.type == F_OUTFLOW_P ? 1.0 : -1.0;
+          for (int i = gc; i < NE; i += nch) {
+            double c = sg * (double)FL[i * NA + gb] * tb.dGam[i];
             tn += c;
             te += c * tb.eps[i] * (double)S.u0s[gb];
           }
@@ -1078,8 +1150,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
       T* EP = EB + 2 * nbin;
       T* EQ = EB + 3 * nbin;
       if (gact) {
-        if (F.own & 1) energy_column<T, T>(gc, nch, NE, NA, gb, em[4], ew[4], FL, EP);
-        if (F.own & 2) energy_column<T, T>(gc, nch, NE, NA, gb, em[5], ew[5], FL, EQ);
+        if (F.own & 1) energy_column<T, T>(gc, nch, NE, NA, gb, em[4], ew[4], FL, EP, T(1), P3);
+        if (F.own & 2) energy_column<T, T>(gc, nch, NE, NA, gb, em[5], ew[5], FL, EQ, T(1), P3);
       }
       __syncthreads();
       if (gact) {
@@ -1104,15 +1176,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
       float bk = -1.0f;
       int bi = 0x7fffffff;
       for (int q = tid; q < nbin; q += kThreads) {
-        part = ff_add(part, (float)dNs[q]);
-        float k = fabsf((float)dNs[q]);
+        const float c = (float)dNs[q] * (float)S.dGam[q / NA];
+        part = ff_add(part, two_prod((float)dNs[q], (float)S.dGam[q / NA]));
+        float k = fabsf(c);
         if (k > bk) { bk = k; bi = q; }
       }
       ff tot = block_sum_ff(part, S.redf);
       int at = block_argmax(bk, bi, S.rkey, S.ridx);
       if (tid == 0) {
         ff c = ff_add(S.dtot[s], ff_neg(tot));
-        S.corr[s] = ff_to_d(c);
+        S.corr[s] = ff_to_d(c) / tb.dGam[at / NA];   // back to content per unit dGamma
         S.corr_at[s] = at;
       }
     }
@@ -1121,6 +1194,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
   }
 
   // --- implicit collision per (species, group) (Sec. 3.5) and moments (Eq. hydrosource)
+  //     f* = f + dN / (phi^6 dV u0 dGamma dOmega); D_b = 1 + (ka+ks) tau_b,
+  //     J = sum dOm r/D / sum dOm (1 + ka tau)/D, f = (r + ks tau J)/D
   const double alz = st.al[zone], c6z = pow6(st.cf[zone]), volz = tb.vol[zone];
   const double rdt = 1.0 / dt;
   {
@@ -1133,7 +1208,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
       double u0 = gz * (1.0 + nv);
       S.zu0[ang] = u0;
       S.ztau[ang] = alz * dt / u0;
-      S.zcn[ang] = 1.0 / (c6z * volz * u0 * tb.dOm[ang]);
+      S.zcn[ang] = 1.0 / (c6z * volz * u0 * tb.dOm[ang]);   // dN is per unit dGamma
+      S.zt_f[ang] = ff_from_d(S.ztau[ang]);
+      S.zc_f[ang] = ff_from_d(S.zcn[ang]);
+      S.zd_f[ang] = ff_from_d(tb.dOm[ang]);
+      S.zq_f[ang] = (float)(c6z * u0 * tb.dOm[ang] * rdt);
     }
   }
   __syncthreads();
@@ -1141,52 +1220,104 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     const int s = row / NE, i = row % NE;
     const size_t oz = ((size_t)s * tb.n_zone + zone) * NE + i;
     const double ka = st.ka[oz], ks = st.ks[oz], fe = st.fe[oz];
-    const double kt = ka + ks, kafe = ka * fe, rdg = 1.0 / tb.dGam[i];
     const T* fz = fin + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
     const DN* dn = S.dN + (size_t)s * nbin + (size_t)i * NA;
     const int cat = S.corr_at[s] - i * NA;       // corrected bin of this row, if any
     const double cval = S.corr[s];
-    double* rr = S.wr_r + (size_t)warp * NA;
-    double* ri = S.wr_i + (size_t)warp * NA;
-    double sr = 0.0, s1 = 0.0;
-    for (int ang = lane; ang < NA; ang += 32) {
-      double tau = S.ztau[ang];
-      double dnv = (double)dn[ang] + (ang == cat ? cval : 0.0);
-      double fst = (double)fz[ang] + dnv * S.zcn[ang] * rdg;
-      double r = fst + tau * kafe;
-      double iD = 1.0 / (1.0 + kt * tau);
-      rr[ang] = fst;
-      ri[ang] = iD;
-      double dom = tb.dOm[ang];
-      sr += dom * r * iD;
-      s1 += dom * (1.0 + ka * tau) * iD;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    const double J = sr / s1;
-    double mN = 0.0, mE = 0.0, mP0 = 0.0, mP1 = 0.0, mP2 = 0.0;
-    int bad = 0;
     T* fo = fout + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
     const double cdg = c6z * tb.dGam[i] * rdt;
-    for (int ang = lane; ang < NA; ang += 32) {
-      double tau = S.ztau[ang];
-      double fst = rr[ang];
-      double r = fst + tau * kafe;
-      double fn = (r + ks * tau * J) * ri[ang];
-      T fw = (T)fn;
-      fo[ang] = fw;
-      bad |= !isfinite(fn);
-      // collision moments in the arithmetic type (float64 path: float64)
-      T dc = (T)(cdg * S.zu0[ang] * tb.dOm[ang] * ((double)fw - fst));
-      mN += (double)dc;
-      T de = dc * (T)tb.eps[i];
-      mE += (double)de;
-      mP0 += (double)(de * S.n0[ang]);
-      mP1 += (double)(de * S.n1[ang]);
-      mP2 += (double)(de * S.n2[ang]);
+    double mN = 0.0, mE = 0.0, mP0 = 0.0, mP1 = 0.0, mP2 = 0.0;
+    int bad = 0;
+    if constexpr (sizeof(T) == 8) {
+      const double kt = ka + ks, kafe = ka * fe;
+      double* rr = S.wr_r + (size_t)warp * NA;
+      double* ri = S.wr_i + (size_t)warp * NA;
+      double sr = 0.0, s1 = 0.0;
+      for (int ang = lane; ang < NA; ang += 32) {
+        double tau = S.ztau[ang];
+        double dnv = (double)dn[ang] + (ang == cat ? cval : 0.0);
+        double fst = (double)fz[ang] + dnv * S.zcn[ang];
+        double r = fst + tau * kafe;
+        double iD = 1.0 / (1.0 + kt * tau);
+        rr[ang] = fst;
+        ri[ang] = iD;
+        double dom = tb.dOm[ang];
+        sr += dom * r * iD;
+        s1 += dom * (1.0 + ka * tau) * iD;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      const double J = sr / s1;
+      for (int ang = lane; ang < NA; ang += 32) {
+        double tau = S.ztau[ang];
+        double fst = rr[ang];
+        double r = fst + tau * kafe;
+        double fn = (r + ks * tau * J) * ri[ang];
+        fo[ang] = (T)fn;
+        bad |= !isfinite(fn);
+        double dc = cdg * S.zu0[ang] * tb.dOm[ang] * (fn - fst);
+        mN += dc;
+        double de = dc * tb.eps[i];
+        mE += de;
+        mP0 += de * (double)S.n0[ang];
+        mP1 += de * (double)S.n1[ang];
+        mP2 += de * (double)S.n2[ang];
+      }
+    } else {
+      // mixed path: double-float (about 48-bit) arithmetic on the FP32 pipes
+      // keeps the solve conservative to well below 1e-10 where float32 would
+      // not, at a fraction of GB300's float64 cost
+      const ff ka_f = ff_from_d(ka), ks_f = ff_from_d(ks);
+      const ff kt_f = ff_from_d(ka + ks), kafe_f = ff_from_d(ka * fe);
+      float* buf = reinterpret_cast<float*>(S.wr_r) + (size_t)warp * 4 * NA;   // fst.hi, fst.lo, iD.hi, iD.lo
+      ff sr = ff{0.0f, 0.0f}, s1 = ff{0.0f, 0.0f};
+      for (int ang = lane; ang < NA; ang += 32) {
+        const ff tau = S.zt_f[ang];
+        const ff zcn = S.zc_f[ang];
+        const ff dom = S.zd_f[ang];
+        ff dnv = ff{(float)dn[ang], 0.0f};
+        if (ang == cat) dnv = ff_add(dnv, ff_from_d(cval));
+        const ff fst = ff_add(ff{(float)fz[ang], 0.0f}, ff_mul(zcn, dnv));
+        const ff r = ff_add(fst, ff_mul(tau, kafe_f));
+        const ff iD = ff_recip(ff_add(ff{1.0f, 0.0f}, ff_mul(kt_f, tau)));
+        buf[4 * ang] = fst.hi; buf[4 * ang + 1] = fst.lo;
+        buf[4 * ang + 2] = iD.hi; buf[4 * ang + 3] = iD.lo;
+        const ff domD = ff_mul(dom, iD);
+        sr = ff_add(sr, ff_mul(domD, r));
+        s1 = ff_add(s1, ff_mul(domD, ff_add(ff{1.0f, 0.0f}, ff_mul(ka_f, tau))));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr = ff_add(sr, ff_shfl_xor(sr, o));
+        s1 = ff_add(s1, ff_shfl_xor(s1, o));
+      }
+      const ff J = ff_mul(sr, ff_recip(s1));
+      const ff ksJ = ff_mul(ks_f, J);
+      float fN = 0.0f, fE = 0.0f, fP0 = 0.0f, fP1 = 0.0f, fP2 = 0.0f;
+      const float eps_i = (float)tb.eps[i];
+      const float dg_i = (float)tb.dGam[i];
+      for (int ang = lane; ang < NA; ang += 32) {
+        const ff tau = S.zt_f[ang];
+        const ff fst = ff{buf[4 * ang], buf[4 * ang + 1]};
+        const ff iD = ff{buf[4 * ang + 2], buf[4 * ang + 3]};
+        const ff r = ff_add(fst, ff_mul(tau, kafe_f));
+        const ff fn = ff_mul(ff_add(r, ff_mul(tau, ksJ)), iD);
+        const float fw = fn.hi + fn.lo;
+        fo[ang] = fw;
+        bad |= !isfinite(fw);
+        const ff del = ff_add(ff{fw, 0.0f}, ff_neg(fst));
+        const float dc = S.zq_f[ang] * dg_i * (del.hi + del.lo);
+        fN += dc;
+        const float de = dc * eps_i;
+        fE += de;
+        fP0 += de * (float)S.n0[ang];
+        fP1 += de * (float)S.n1[ang];
+        fP2 += de * (float)S.n2[ang];
+      }
+      mN = fN; mE = fE; mP0 = fP0; mP1 = fP1; mP2 = fP2;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1234,7 +1365,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RemapSmem {
-  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam;
+  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3;
   Wt<T>* W; AEnt<T>* ent; short* off; int* cnt;
   ff* redf; float* rkey; int* ridx;
 };
@@ -1257,6 +1388,7 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(n2, T, nang);
   BT_TAKE(dOm, T, nang);
   BT_TAKE(dGam, T, ne);
+  BT_TAKE(p3, T, 2 * ne + 3);
   BT_TAKE(W, Wt<T>, nang);
   BT_TAKE(ent, AEnt<T>, 4 * nang);
   BT_TAKE(off, short, nang + 1);
@@ -1289,11 +1421,15 @@ __global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
     S.dOm[q] = (T)tb.dOm[q];
   }
   for (int q = tid; q < NE; q += kThreads) S.dGam[q] = (T)tb.dGam[q];
+  for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = (T)tb.p3[q];
   __syncthreads();
+  const T* P3 = S.p3 + NE + 1;
   Loc<T> X, Y;
   make_loc(X, st.v_old + 3 * zone, st.al_old[zone], st.cf_old[zone]);
   make_loc(Y, st.v + 3 * zone, st.al[zone], st.cf[zone]);
-  for (int ang = tid; ang < NA; ang += kThreads) chain_weights(tb, S.mu, X, Y, nullptr, 0, AX_TIME, ang, S.W[ang]);
+  const T Rg = (T)tb.R;
+  for (int ang = tid; ang < NA; ang += kThreads)
+    chain_weights(tb, S.mu, S.n0, S.n1, S.n2, X, Y, (const T*)nullptr, 0, AX_TIME, ang, Rg, S.W[ang]);
   __syncthreads();
   const int em = gact ? S.W[gb].m : 0;
   const T ew = gact ? S.W[gb].we : T(0);
@@ -1302,35 +1438,49 @@ __global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
   T* f = reinterpret_cast<T*>(st.f);
   for (int s = 0; s < tb.n_s; ++s) {
     T* fz = f + ((size_t)s * tb.n_zone + zone) * nbin;
+    // content per unit dGamma of the old frame: y = phi^6 u0 dOmega f
     ff part = ff{0.0f, 0.0f};
     if (gact) {
       const T u0 = X.g * (T(1) + (X.v[0] * S.n0[gb] + X.v[1] * S.n1[gb] + X.v[2] * S.n2[gb]));
       const T cang = c6x * u0 * S.dOm[gb];
       for (int i = gc; i < NE; i += nch) {
         const int q = i * NA + gb;
-        T d = cang * S.dGam[i] * fz[q];
+        T d = cang * fz[q];
         S.src[q] = d;
-        if (sizeof(T) == 4) part = ff_add(part, (float)d);
+        if (sizeof(T) == 4) part = ff_add(part, two_prod((float)d, (float)S.dGam[i]));
       }
     }
     ff tot_in = ff{0.0f, 0.0f};
     if (sizeof(T) == 4) tot_in = block_sum_ff(part, S.redf);
     else __syncthreads();
-    if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, S.src, S.E);
+    if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, S.src, S.E, T(1), P3);
     __syncthreads();
     if (gact) angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
     __syncthreads();
     int at = -1;
-    ff corr = ff{0.0f, 0.0f};
-    if (sizeof(T) == 4) corr = conservation_residual(S.dst, nbin, tot_in, S.redf, S.rkey, S.ridx, &at);
+    double corr_y = 0.0;
+    if (sizeof(T) == 4) {
+      // restore the exact content total of the zone (float gathers round)
+      ff partc = ff{0.0f, 0.0f};
+      float bk = -1.0f;
+      int bi = 0x7fffffff;
+      for (int q = tid; q < nbin; q += kThreads) {
+        partc = ff_add(partc, two_prod((float)S.dst[q], (float)S.dGam[q / NA]));
+        float k = fabsf((float)S.dst[q] * (float)S.dGam[q / NA]);
+        if (k > bk) { bk = k; bi = q; }
+      }
+      ff tot = block_sum_ff(partc, S.redf);
+      at = block_argmax(bk, bi, S.rkey, S.ridx);
+      corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
+    }
     if (gact) {
       const T u0 = Y.g * (T(1) + (Y.v[0] * S.n0[gb] + Y.v[1] * S.n1[gb] + Y.v[2] * S.n2[gb]));
       const T cang = c6y * u0 * S.dOm[gb];
       for (int ip = gc; ip < NE; ip += nch) {
         const int q = ip * NA + gb;
         T d = S.dst[q];
-        if (q == at) d = (T)((double)d + ff_to_d(corr));
-        fz[q] = d / (cang * S.dGam[ip]);
+        if (q == at) d = (T)((double)d + corr_y);
+        fz[q] = d / cang;
       }
     }
     __syncthreads();
