@@ -8,6 +8,11 @@ zone-group-angle updates per second (species included) of a full step.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config3]
                   [--precision mixed|fp64] [--impl ours|reference]
 
+--workload config5 runs the batched form: three independent 2D problems of
+uneven size (128x32, 256x64, 512x128 zones; 8, 12, 20 groups; 48, 80, 128
+angles; 6 species) advanced by one CUDA-graph launch per step; its units are
+the bins of all three problems.
+
 --impl reference times the FP64 CPU oracle (single thread) on a bounded
 sample of zones of the same workload.  Under torchrun (N > 1) every rank runs
 an independent replica; rank 0 prints one JSON line.
@@ -155,6 +160,8 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     build.build()
+    if args.workload == "config5":
+        return run_batch(args, rank, world)
     prob = W.by_name(args.workload)
     mixed = args.precision == "mixed"
     stream = torch.cuda.Stream()
@@ -169,6 +176,8 @@ def run_ours(args):
     t.set_background(B[0])
     t.set_f(prob.f0)
     dt = t.max_dt(prob.cfl)
+    if args.autotune:
+        t.autotune(dt)
     bins = prob.n_bins
     units_per_step = bins
 
@@ -262,6 +271,7 @@ def run_ours(args):
             "l2": "inputs larger than L2 (f is %.0f MB per buffer)" % (bins * (4 if mixed else 8) / 1e6),
             "parallelism": "replicas" if world > 1 else "single GPU",
             "backgrounds": "B0/B1 alternate every step (time remap active)",
+            "launch_shape": t.launch_shape,
         },
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -284,12 +294,200 @@ def run_ours(args):
                     "frac": achieved_gbs / peak, "algorithmic_bytes_per_bin": bpb},
         },
     }
+    if mixed and not args.no_fp64_compare:
+        t.close()
+        del t
+        ms64 = time_fp64_path(prob, dev)
+        res["vs_fp64_gpu"] = {"value": units_per_step / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                              "speedup": ms64 / ms,
+                              "what": "the same step in plain FP64 on this GPU (same kernels, T = double)"}
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def time_fp64_path(prob, dev, steps=5, warmup=3):
+    """ms per step of the plain FP64 path on the same workload and device
+    backgrounds (events on its own stream)."""
+    import torch
+    from paper_2003_02845_gb300 import bt
+    stream = torch.cuda.Stream()
+    t = bt.Transport(prob, "fp64", stream=stream)
+    t.set_background(prob.backgrounds[0])
+    t.set_f(prob.f0)
+    dt = t.max_dt(prob.cfl)
+    for k in range(warmup):
+        t.set_background_device(*dev[(k + 1) % 2])
+        t.step(dt)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(steps):
+        t.set_background_device(*dev[(warmup + k + 1) % 2])
+        t.step(dt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    t.close()
+    return ms
+
+
+def run_batch(args, rank, world):
+    """The batched form: every member's step in one CUDA-graph launch."""
+    import torch
+    from paper_2003_02845_gb300 import bt, workloads as W
+    probs = W.config5_problems()
+    mixed = args.precision == "mixed"
+    stream = torch.cuda.Stream()
+    b = bt.Batch(probs, args.precision, stream=stream)
+    dev, dts = [], []
+    for m, p in zip(b.members, probs):
+        dev.append([[torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+                     for x in (bg.v, bg.alpha, bg.phi, bg.kappa_a, bg.kappa_s, bg.f_eq)] for bg in p.backgrounds])
+        m.set_background(p.backgrounds[0])
+        m.set_f(p.f0)
+        dts.append(m.max_dt(p.cfl))
+    shapes = []
+    for m, d, dt in zip(b.members, dev, dts):
+        shapes.append(m.autotune(dt) if args.autotune else m.launch_shape)
+    torch.cuda.synchronize()
+    bins = sum(p.n_bins for p in probs)
+
+    def one_step(k):
+        for m, d in zip(b.members, dev):
+            m.set_background_device(*d[(k + 1) % 2])
+        b.step(dts)
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    l0, g0 = b.launch_count, b.graph_launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.steps):
+            one_step(args.warmup + k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches, graphs = b.launch_count - l0, b.graph_launches - g0
+    if world > 1:
+        x = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        ms = float(x.item())
+        torch.distributed.barrier()
+
+    # end to end: pinned host backgrounds in, every member's source terms out
+    L = bt.lib()
+    pinned, outs = [], []
+    for p in probs:
+        pinned.append([[torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).pin_memory()
+                        for x in (bg.rho, bg.T, bg.Ye, bg.v, bg.alpha, bg.phi, bg.shift,
+                                  bg.kappa_a, bg.kappa_s, bg.f_eq)] for bg in p.backgrounds])
+        S, Z = p.n_species, p.n_zone
+        outs.append([torch.empty(sh, dtype=torch.float64).pin_memory() for sh in ((S, Z), (S, Z), (S, Z, 3), (Z,))])
+    h2d = sum(x.numel() * 8 for pm in pinned for x in pm[0][3:6] + pm[0][7:10])
+    d2h = sum(x.numel() * 8 for o in outs for x in o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        for m, pm in zip(b.members, pinned):
+            bt._check(L.bt_set_background(m.h, bt.BT_MEM_HOST, *[x.data_ptr() for x in pm[(k + 1) % 2]]))
+        b.step(dts)
+        for m, o in zip(b.members, outs):
+            bt._check(L.bt_moments(m.h, bt.BT_MEM_HOST, *[x.data_ptr() for x in o]))
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        x = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(x.item())
+
+    # the dominant kernel: the flux kernel of the largest member, timed alone
+    big = max(range(len(probs)), key=lambda i: probs[i].n_bins)
+    m, p = b.members[big], probs[big]
+    m.profile(True)
+    for k in range(args.steps):
+        m.set_background_device(*dev[big][(k + 1) % 2])
+        m.step(dts[big])
+    flux_ms, flux_n = m.profile_read(bt.K_FLUX)
+    m.profile(False)
+    flux_avg_ms = flux_ms / max(flux_n, 1)
+    fpb = algorithmic_flops_per_bin(p)
+    bpb = algorithmic_bytes_per_bin(p, mixed)
+    achieved_tf = p.n_bins * fpb / (flux_avg_ms * 1e-3) / 1e12
+    achieved_gbs = p.n_bins * bpb / (flux_avg_ms * 1e-3) / 1e9
+    peak_tf = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    peaks, peak_src = load_peaks()
+    peak = hbm_peak(peaks)
+    res = {
+        "metric": METRIC,
+        "value": world * bins / (ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if mixed else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "config5_batched_3x2d_6species",
+            "problems": [p.name for p in probs],
+            "precision": args.precision + (" (f32 f/fluxes/remap, f64 collision and sums)" if mixed else ""),
+            "bins_per_step": bins,
+            "launch_shapes": shapes,
+            "graph_launches_per_step": graphs / args.steps,
+            "l2": "inputs larger than L2 (f is %.0f MB per buffer)" % (bins * (4 if mixed else 8) / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "backgrounds": "B0/B1 alternate every step (time remap active)",
+        },
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": {"value": world * bins / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {
+            "kernel": "k_flux_collide<%s> of %s" % ("float" if mixed else "double", p.name),
+            "bound": "alu",
+            "achieved": achieved_tf,
+            "peak": peak_tf,
+            "peak_source": "derived: %d SMs x %d FP32 lanes x 2 x %.2f GHz%s" % (
+                GB300_SMS, GB300_FP32_LANES, GB300_SM_GHZ, "" if mixed else " / 64 (float64)"),
+            "unit": "TFLOP/s",
+            "frac": achieved_tf / peak_tf,
+            "traffic": None,
+            "algorithmic_flops_per_bin": fpb,
+            "avg_launch_ms": flux_avg_ms,
+            "hbm": {"achieved": achieved_gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                    "frac": achieved_gbs / peak, "algorithmic_bytes_per_bin": bpb},
+        },
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline_multi(probs, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    b.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline_multi(probs, budget_s):
+    """The oracle on a sample of every problem of a batch, budget split by
+    bins; value = sampled bins / seconds."""
+    tot = sum(p.n_bins for p in probs)
+    done, spent, parts = 0.0, 0.0, []
+    for p in probs:
+        r = cpu_baseline(p, max(1.0, budget_s * p.n_bins / tot))
+        done += r["bins"]
+        spent += r["seconds"]
+        parts.append(r["sample"])
+    return {"value": done / spent, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "; ".join(parts)}
 
 
 def cpu_baseline(prob, budget_s=15.0, steps=1):
@@ -315,6 +513,7 @@ def cpu_baseline(prob, budget_s=15.0, steps=1):
         if n >= prob.n_zone and spent > 0.2 * budget_s:
             break
     return {"value": done_bins / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds": spent, "bins": done_bins,
             "sample": "%d zone updates (all species, groups, angles) of %s by the single-threaded FP64 "
                       "oracle in %.1f s, static background (time remap not in the sample)"
                       % (done_bins // (prob.n_species * prob.n_eps * prob.n_ang), prob.name, spent)}
@@ -325,6 +524,8 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2003_02845_gb300 import workloads as W
+    if args.workload == "config5":
+        return run_reference_multi(args, W.config5_problems())
     prob = W.by_name(args.workload)
     per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
@@ -342,6 +543,24 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def run_reference_multi(args, probs):
+    per_step = max(3.0, 60.0 / max(args.steps + args.warmup, 1))
+    bins = sum(p.n_bins for p in probs)
+    for _ in range(args.warmup):
+        cpu_baseline_multi(probs, 3.0)
+    vals = [cpu_baseline_multi(probs, per_step) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    res = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": bins / v * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "config5_batched_3x2d_6species", "precision": "fp64 oracle (CPU)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,6 +571,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="pick each problem's launch shape by timing")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -171,6 +171,41 @@ enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2 };
 int bt_profile(bt_handle* h, int enable);
 int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launches);
 
+/* Launch shape of the fused flux kernel: threads per CTA (128, 256 or 512;
+ * default 256, or the choice cached by the autotuner).  The arithmetic of a
+ * step does not depend on it. */
+int bt_launch_shape(const bt_handle* h, int* threads_per_cta);
+int bt_set_launch_shape(bt_handle* h, int threads_per_cta);
+
+/* Autotuner: times the flux kernel of the current state (background and f
+ * set) for every launch shape that fits, keeps the fastest, and -- if the
+ * environment variable BT_TUNE_CACHE names a file -- records it there under a
+ * key of the problem shape; bt_create reads that file.  The timing launches
+ * overwrite the last-step moments but not f.  *chosen_nt may be NULL. */
+int bt_autotune(bt_handle* h, double dt, int* chosen_nt);
+
+/* Batched step: n independent problems (each its own configuration, e.g. of
+ * uneven size and group/angle counts) advanced together.  bt_batch_create
+ * creates one member handle per configuration, all on `stream`; the members
+ * are set and read through the single-problem calls above (bt_batch_member
+ * returns member i's handle, owned by the batch).  bt_batch_step(b, dt[n])
+ * advances every member by one step (Sec. 3.3, 3.5) with ONE launch of a CUDA
+ * graph whose branches run the members' kernels concurrently; graphs are
+ * captured on first use and cached by the members' buffer parity, pending
+ * time remap, dt and launch shape (at most 16 graphs are kept).  `stream`
+ * must be a created stream: the legacy default stream (0) cannot be
+ * captured and gives BT_ERR_ARG.  A member without a background gives
+ * BT_ERR_STATE, a dt[i] <= 0 or non-finite BT_ERR_DT; neither launches
+ * anything.  Errors inside the kernels surface, as for bt_step, at the next
+ * call that returns data for that member. */
+typedef struct bt_batch bt_batch;
+int bt_batch_create(const bt_config* cfgs, int n, void* stream, bt_batch** out);
+int bt_batch_member(bt_batch* b, int i, bt_handle** out);
+int bt_batch_step(bt_batch* b, const double* dt);
+int64_t bt_batch_launch_count(const bt_batch* b);   /* kernel launches of all members */
+int64_t bt_batch_graph_launches(const bt_batch* b);
+int bt_batch_destroy(bt_batch* b);
+
 /* Weighted totals of a distribution without any device allocation.
  * The paper has no counterpart: this is a library service for callers that
  * cannot allocate device memory -- e.g. a host code whose own allocator owns

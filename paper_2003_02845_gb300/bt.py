@@ -65,6 +65,17 @@ def lib():
         L.bt_launch_count.restype = C.c_int64
         L.bt_launch_count.argtypes = [vp]
         L.bt_weighted_totals_noalloc.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp, vp, vp]
+        L.bt_autotune.argtypes = [vp, C.c_double, C.POINTER(C.c_int)]
+        L.bt_launch_shape.argtypes = [vp, C.POINTER(C.c_int)]
+        L.bt_set_launch_shape.argtypes = [vp, i32]
+        L.bt_batch_create.argtypes = [C.POINTER(BtConfig), i32, vp, C.POINTER(vp)]
+        L.bt_batch_member.argtypes = [vp, i32, C.POINTER(vp)]
+        L.bt_batch_step.argtypes = [vp, C.POINTER(C.c_double)]
+        L.bt_batch_launch_count.restype = C.c_int64
+        L.bt_batch_launch_count.argtypes = [vp]
+        L.bt_batch_graph_launches.restype = C.c_int64
+        L.bt_batch_graph_launches.argtypes = [vp]
+        L.bt_batch_destroy.argtypes = [vp]
         L.bt_profile.argtypes = [vp, i32]
         L.bt_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         _lib = L
@@ -88,6 +99,33 @@ def _host64(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
+def make_config(prob, precision: str, stream_handle: int, phase_norm: float = 1.0, keep=None):
+    """bt_config for a workloads.Problem; host arrays are appended to `keep`."""
+    r = _host64(prob.r_edges)
+    e = _host64(prob.eps_edges)
+    k = np.ascontiguousarray(np.asarray(prob.species_kind, dtype=np.int32))
+    if keep is not None:
+        keep += [r, e, k]
+    cfg = BtConfig()
+    cfg.geom = prob.geom
+    cfg.n_r = prob.n_r
+    cfg.n_theta = prob.n_theta
+    cfg.r_edges = r.ctypes.data_as(C.POINTER(C.c_double))
+    cfg.theta_periodic = int(prob.theta_periodic)
+    cfg.dtheta_column = float(prob.dtheta_column)
+    cfg.dphi_wedge = float(prob.dphi)
+    cfg.n_species = prob.n_species
+    cfg.species_kind = k.ctypes.data_as(C.POINTER(C.c_int32))
+    cfg.n_eps = prob.n_eps
+    cfg.eps_edges = e.ctypes.data_as(C.POINTER(C.c_double))
+    cfg.n_mu = prob.n_mu
+    cfg.n_phi = prob.n_phi
+    cfg.precision = BT_MIXED if precision == "mixed" else BT_FP64
+    cfg.phase_norm = phase_norm
+    cfg.stream = stream_handle
+    return cfg
+
+
 class Transport:
     """One transport problem on the current CUDA device.
 
@@ -95,7 +133,7 @@ class Transport:
     precision: "fp64" or "mixed".
     """
 
-    def __init__(self, prob, precision: str = "fp64", stream=None, phase_norm: float = 1.0):
+    def __init__(self, prob, precision: str = "fp64", stream=None, phase_norm: float = 1.0, _handle=None):
         import torch
         L = lib()
         self.prob = prob
@@ -103,26 +141,13 @@ class Transport:
         self.fdtype = np.float32 if self.mixed else np.float64
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self._r = _host64(prob.r_edges)
-        self._e = _host64(prob.eps_edges)
-        self._k = np.ascontiguousarray(np.asarray(prob.species_kind, dtype=np.int32))
-        cfg = BtConfig()
-        cfg.geom = prob.geom
-        cfg.n_r = prob.n_r
-        cfg.n_theta = prob.n_theta
-        cfg.r_edges = self._r.ctypes.data_as(C.POINTER(C.c_double))
-        cfg.theta_periodic = int(prob.theta_periodic)
-        cfg.dtheta_column = float(prob.dtheta_column)
-        cfg.dphi_wedge = float(prob.dphi)
-        cfg.n_species = prob.n_species
-        cfg.species_kind = self._k.ctypes.data_as(C.POINTER(C.c_int32))
-        cfg.n_eps = prob.n_eps
-        cfg.eps_edges = self._e.ctypes.data_as(C.POINTER(C.c_double))
-        cfg.n_mu = prob.n_mu
-        cfg.n_phi = prob.n_phi
-        cfg.precision = BT_MIXED if self.mixed else BT_FP64
-        cfg.phase_norm = phase_norm
-        cfg.stream = self.stream.cuda_stream
+        self.shape = (prob.n_species, prob.n_zone, prob.n_eps, prob.n_ang)
+        if _handle is not None:          # a batch member: owned by the batch
+            self.h = _handle
+            self.owned = False
+            return
+        self._keep = []
+        cfg = make_config(prob, precision, self.stream.cuda_stream, phase_norm, self._keep)
         self.cfg = cfg
         nbytes = L.bt_workspace_bytes(C.byref(cfg))
         if nbytes == 0:
@@ -134,12 +159,12 @@ class Transport:
         h = C.c_void_p()
         _check(L.bt_create(C.byref(cfg), C.c_void_p(aligned), C.byref(h)))
         self.h = h
-        self.shape = (prob.n_species, prob.n_zone, prob.n_eps, prob.n_ang)
+        self.owned = True
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "owned", False):
             lib().bt_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -210,6 +235,20 @@ class Transport:
     def launch_count(self) -> int:
         return int(lib().bt_launch_count(self.h))
 
+    def autotune(self, dt: float) -> int:
+        nt = C.c_int()
+        _check(lib().bt_autotune(self.h, float(dt), C.byref(nt)))
+        return nt.value
+
+    @property
+    def launch_shape(self) -> int:
+        nt = C.c_int()
+        _check(lib().bt_launch_shape(self.h, C.byref(nt)))
+        return nt.value
+
+    def set_launch_shape(self, nt: int):
+        _check(lib().bt_set_launch_shape(self.h, int(nt)))
+
     def profile(self, enable: bool):
         _check(lib().bt_profile(self.h, int(enable)))
 
@@ -220,6 +259,58 @@ class Transport:
 
 
 K_TIME_REMAP, K_FLUX, K_OUTFLOW = 0, 1, 2
+
+
+class Batch:
+    """Several independent problems advanced by one CUDA-graph launch per
+    step (bt_batch_* in include/bt.h).  ``members[i]`` is a Transport view of
+    problem i for backgrounds, f and outputs."""
+
+    def __init__(self, probs, precision="mixed", stream=None):
+        import torch
+        L = lib()
+        self.probs = list(probs)
+        # the step is captured into a CUDA graph, which the legacy default
+        # stream does not allow: without a stream, the batch makes its own
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._keep = []
+        n = len(self.probs)
+        cfgs = (BtConfig * n)()
+        for i, p in enumerate(self.probs):
+            cfgs[i] = make_config(p, precision, self.stream.cuda_stream, 1.0, self._keep)
+        h = C.c_void_p()
+        _check(L.bt_batch_create(cfgs, n, self.stream.cuda_stream, C.byref(h)))
+        self.h = h
+        self.members = []
+        for i, p in enumerate(self.probs):
+            mh = C.c_void_p()
+            _check(L.bt_batch_member(h, i, C.byref(mh)))
+            self.members.append(Transport(p, precision, stream=self.stream, _handle=mh))
+
+    def step(self, dts):
+        arr = (C.c_double * len(self.members))(*[float(x) for x in dts])
+        _check(lib().bt_batch_step(self.h, arr))
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().bt_batch_launch_count(self.h))
+
+    @property
+    def graph_launches(self) -> int:
+        return int(lib().bt_batch_graph_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            lib().bt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def weighted_totals_noalloc(f, w_za, w_e, precision: str, out, stream=None):

@@ -4,9 +4,15 @@
 // kernels of bt_kernels.cu; this file only prepares tables and launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -147,6 +153,8 @@ struct bt_handle {
   bool has_bg, remap_pending;
   int64_t launches;
   size_t nzone, nbin_total, fbytes;
+  int nt;              // block size of the flux kernel (autotuned)
+  std::string tune_key;
   // profiling: (kernel id, start, stop) per launch while enabled
   bool prof;
   std::vector<int> prof_id;
@@ -237,6 +245,45 @@ int validate(const bt_config* c) {
   }
   if (c->precision != BT_FP64 && c->precision != BT_MIXED) return fail(BT_ERR_ARG, "precision");
   return BT_OK;
+}
+
+// Autotuner cache: one "key nt" pair per line in the file named by the
+// environment variable BT_TUNE_CACHE (nothing is read or written without it).
+std::mutex g_tune_mutex;
+
+std::string tune_key(const bt_config* c) {
+  std::ostringstream k;
+  k << "v1|" << (c->precision == BT_MIXED ? "mixed" : "fp64") << "|g" << c->geom << "|s" << c->n_species << "|e"
+    << c->n_eps << "|mu" << c->n_mu << "|ph" << c->n_phi << "|z" << (long)c->n_r * c->n_theta;
+  return k.str();
+}
+
+int tune_lookup(const std::string& key) {
+  const char* path = std::getenv("BT_TUNE_CACHE");
+  if (!path) return 0;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  std::ifstream in(path);
+  std::string k;
+  int nt = 0, found = 0;
+  while (in >> k >> nt)
+    if (k == key) found = nt;
+  return found;
+}
+
+void tune_store(const std::string& key, int nt) {
+  const char* path = std::getenv("BT_TUNE_CACHE");
+  if (!path) return;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  std::map<std::string, int> all;
+  {
+    std::ifstream in(path);
+    std::string k;
+    int v;
+    while (in >> k >> v) all[k] = v;
+  }
+  all[key] = nt;
+  std::ofstream out(path, std::ios::trunc);
+  for (auto& kv : all) out << kv.first << " " << kv.second << "\n";
 }
 
 }  // namespace
@@ -403,8 +450,20 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   h->prof = false;
   h->has_bg = false;
   h->remap_pending = false;
+  // launch shape: cached autotuner choice, else 256 threads per CTA
+  {
+    int pe = bt::prepare_kernels();
+    if (pe) { bt_destroy(h); return cuda_fail((cudaError_t)pe, "cudaFuncSetAttribute"); }
+  }
+  h->tune_key = tune_key(c);
+  h->nt = 256;
+  {
+    int cached = tune_lookup(h->tune_key);
+    if ((cached == 128 || cached == 256 || cached == 512) && bt::flux_occupancy(T, h->mixed, cached) > 0)
+      h->nt = cached;
+  }
   // shared memory per CTA must fit the opt-in limit
-  size_t need = std::max(bt::flux_smem_bytes(T, h->mixed), bt::remap_smem_bytes(T, h->mixed));
+  size_t need = std::max(bt::flux_smem_bytes(T, h->mixed, h->nt), bt::remap_smem_bytes(T, h->mixed));
   int lim = bt::max_optin_smem();
   if ((long)need > (long)lim) {
     bt_destroy(h);
@@ -543,10 +602,8 @@ int bt_max_dt(bt_handle* h, double cfl, double* dt_out) {
   return BT_OK;
 }
 
-int bt_step(bt_handle* h, double dt) {
-  if (!h) return fail(BT_ERR_ARG, "NULL");
-  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_step before bt_set_background");
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BT_ERR_DT, "dt must be positive and finite");
+// Enqueue one step's kernels on h->stream (also used inside graph capture).
+static int step_enqueue(bt_handle* h, double dt) {
   bind_state(h);
   int e;
   if (h->remap_pending) {
@@ -558,7 +615,7 @@ int bt_step(bt_handle* h, double dt) {
   }
   {
     ProfScope ps(h, BT_K_FLUX);
-    e = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, h->stream);
+    e = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, h->nt, h->stream);
     h->launches += 1;
     if (e) return cuda_fail((cudaError_t)e, "flux/collide");
   }
@@ -569,6 +626,67 @@ int bt_step(bt_handle* h, double dt) {
     if (e) return cuda_fail((cudaError_t)e, "outflow");
   }
   h->fcur = 1 - h->fcur;
+  return BT_OK;
+}
+
+int bt_step(bt_handle* h, double dt) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_step before bt_set_background");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BT_ERR_DT, "dt must be positive and finite");
+  return step_enqueue(h, dt);
+}
+
+int bt_autotune(bt_handle* h, double dt, int* chosen_nt) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_autotune before bt_set_background");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BT_ERR_DT, "dt must be positive and finite");
+  bind_state(h);
+  const int cand[3] = {128, 256, 512};
+  const int lim = bt::max_optin_smem();
+  float best = 0.f;
+  int best_nt = h->nt;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int nt : cand) {
+    if ((long)bt::flux_smem_bytes(h->tb, h->mixed, nt) > (long)lim) continue;
+    if (bt::flux_occupancy(h->tb, h->mixed, nt) <= 0) continue;
+    // the flux kernel reads f and writes the other buffer (and the moments),
+    // so repeated launches leave the state unchanged
+    int e = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, nt, h->stream);
+    if (e) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail((cudaError_t)e, "autotune"); }
+    cudaEventRecord(a, h->stream);
+    for (int k = 0; k < 3; ++k) bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, nt, h->stream);
+    cudaEventRecord(b, h->stream);
+    cudaError_t ce = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, b);
+    if (ce != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(ce, "autotune timing"); }
+    h->launches += 4;
+    if (best == 0.f || ms < best) { best = ms; best_nt = nt; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->nt = best_nt;
+  tune_store(h->tune_key, best_nt);
+  if (chosen_nt) *chosen_nt = best_nt;
+  return check_flag(h);
+}
+
+int bt_launch_shape(const bt_handle* h, int* threads_per_cta) {
+  if (!h || !threads_per_cta) return fail(BT_ERR_ARG, "NULL");
+  *threads_per_cta = h->nt;
+  return BT_OK;
+}
+
+int bt_set_launch_shape(bt_handle* h, int threads_per_cta) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  if (threads_per_cta != 128 && threads_per_cta != 256 && threads_per_cta != 512)
+    return fail(BT_ERR_ARG, "threads_per_cta must be 128, 256 or 512");
+  if ((long)bt::flux_smem_bytes(h->tb, h->mixed, threads_per_cta) > (long)bt::max_optin_smem() ||
+      bt::flux_occupancy(h->tb, h->mixed, threads_per_cta) <= 0)
+    return fail(BT_ERR_ARG, "launch shape does not fit this problem");
+  h->nt = threads_per_cta;
   return BT_OK;
 }
 
@@ -635,6 +753,133 @@ int bt_jhk(bt_handle* h, int mem, double* J, double* H, double* K) {
 }
 
 int64_t bt_launch_count(const bt_handle* h) { return h ? h->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Batched step: many independent problems advanced by one graph launch.
+// ---------------------------------------------------------------------------
+struct bt_batch {
+  std::vector<bt_handle*> m;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  std::map<std::vector<double>, cudaGraphExec_t> graphs;
+  int64_t graph_launches = 0;
+};
+
+int bt_batch_destroy(bt_batch* b) {
+  if (!b) return BT_OK;
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+  for (bt_handle* h : b->m) bt_destroy(h);
+  delete b;
+  return BT_OK;
+}
+
+int bt_batch_create(const bt_config* cfgs, int n, void* stream, bt_batch** out) {
+  if (!cfgs || n < 1 || !out) return fail(BT_ERR_ARG, "cfgs/n/out");
+  if (!stream) return fail(BT_ERR_ARG, "the batch needs a created stream (graph capture)");
+  *out = nullptr;
+  bt_batch* b = new bt_batch();
+  b->stream = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) {
+    bt_config c = cfgs[i];
+    c.stream = stream;
+    bt_handle* h = nullptr;
+    int rc = bt_create(&c, nullptr, &h);
+    if (rc != BT_OK) { bt_batch_destroy(b); return rc; }
+    b->m.push_back(h);
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { bt_batch_destroy(b); return cuda_fail(e, "batch stream"); }
+    b->side.push_back(st);
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { bt_batch_destroy(b); return cuda_fail(e, "batch event"); }
+    b->join.push_back(ev);
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) { bt_batch_destroy(b); return cuda_fail(e, "batch event"); }
+  *out = b;
+  return BT_OK;
+}
+
+int bt_batch_member(bt_batch* b, int i, bt_handle** out) {
+  if (!b || !out || i < 0 || i >= (int)b->m.size()) return fail(BT_ERR_ARG, "member index");
+  *out = b->m[i];
+  return BT_OK;
+}
+
+int bt_batch_step(bt_batch* b, const double* dt) {
+  if (!b || !dt) return fail(BT_ERR_ARG, "NULL");
+  const int n = (int)b->m.size();
+  std::vector<double> key;
+  for (int i = 0; i < n; ++i) {
+    bt_handle* h = b->m[i];
+    if (!h->has_bg) return fail(BT_ERR_STATE, "batch member without a background");
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return fail(BT_ERR_DT, "dt must be positive and finite");
+    key.push_back(h->cur);
+    key.push_back(h->fcur);
+    key.push_back(h->remap_pending ? 1 : 0);
+    key.push_back(dt[i]);
+    key.push_back(h->nt);
+  }
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    if (b->graphs.size() >= 16) {
+      for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+      b->graphs.clear();
+    }
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    cudaEventRecord(b->fork, b->stream);
+    int rc = BT_OK;
+    for (int i = 0; i < n && rc == BT_OK; ++i) {
+      bt_handle* h = b->m[i];
+      cudaStreamWaitEvent(b->side[i], b->fork, 0);
+      cudaStream_t saved = h->stream;
+      const bool prof = h->prof, pend = h->remap_pending;
+      const int fcur = h->fcur;
+      const int64_t launches = h->launches;
+      h->stream = b->side[i];
+      h->prof = false;
+      rc = step_enqueue(h, dt[i]);
+      // capture records the work; the state advances when the graph runs
+      h->stream = saved; h->prof = prof; h->remap_pending = pend; h->fcur = fcur; h->launches = launches;
+      cudaEventRecord(b->join[i], b->side[i]);
+      cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc != BT_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    it = b->graphs.emplace(key, exec).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  b->graph_launches += 1;
+  for (bt_handle* h : b->m) {
+    h->launches += (h->remap_pending ? 1 : 0) + 3;
+    h->remap_pending = false;
+    h->fcur = 1 - h->fcur;
+  }
+  return BT_OK;
+}
+
+int64_t bt_batch_launch_count(const bt_batch* b) {
+  if (!b) return 0;
+  int64_t n = 0;
+  for (const bt_handle* h : b->m) n += h->launches;
+  return n;
+}
+
+int64_t bt_batch_graph_launches(const bt_batch* b) { return b ? b->graph_launches : 0; }
 
 int bt_profile(bt_handle* h, int enable) {
   if (!h) return fail(BT_ERR_ARG, "NULL");

@@ -78,14 +78,16 @@ struct LaunchCfg {
 // Kernel entry points (bt_kernels.cu).  All enqueue on `stream`; return a
 // cudaError_t as int.
 int launch_time_remap(const Tables& T, const State& S, int mixed, void* stream);
-int launch_flux_collide(const Tables& T, const State& S, double dt, int mixed, void* stream);
+int launch_flux_collide(const Tables& T, const State& S, double dt, int mixed, int nt, void* stream);
 int launch_totals(const Tables& T, const State& S, int mixed, double* d_out /*[2*n_s]*/, void* stream);
 int launch_accumulate_outflow(const Tables& T, const State& S, void* stream);
 int launch_max_rate(const Tables& T, const State& S, double* d_rate /*[1]*/, void* stream);
 int launch_jhk(const Tables& T, const State& S, int mixed, double* J, double* H, double* K, void* stream);
 int launch_check_finite(const Tables& T, const State& S, int mixed, void* stream);
-size_t flux_smem_bytes(const Tables& T, int mixed);
+size_t flux_smem_bytes(const Tables& T, int mixed, int nt);
 size_t remap_smem_bytes(const Tables& T, int mixed);
 int max_optin_smem();
+int prepare_kernels();
+int flux_occupancy(const Tables& T, int mixed, int nt);
 
 }  // namespace bt

@@ -25,8 +25,9 @@ namespace bt {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;   // block size of the non-tuned kernels
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxWarps = 16;    // largest tuned block: 512 threads
 constexpr double kPi = 3.14159265358979323846;
 
 // weights of one source angle for one remap
@@ -347,9 +348,9 @@ template <typename T>
 __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int nmu, int nph, short* off,
                              int* cnt, AEnt<T>* ent) {
   const int tid = threadIdx.x;
-  for (int q = tid; q < nr * na; q += kThreads) cnt[q] = 0;
+  for (int q = tid; q < nr * na; q += (int)blockDim.x) cnt[q] = 0;
   __syncthreads();
-  for (int q = tid; q < nr * na; q += kThreads) {
+  for (int q = tid; q < nr * na; q += (int)blockDim.x) {
     int r = q / na, b = q % na;
     if (!((mask >> r) & 1u)) continue;
     int tgt[4];
@@ -360,7 +361,7 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
   __syncthreads();
   {
     const int warp = tid >> 5, lane = tid & 31;
-    for (int r = warp; r < nr; r += kWarps) {
+    for (int r = warp; r < nr; r += ((int)blockDim.x >> 5)) {
       if (!((mask >> r) & 1u)) continue;
       int per = (na + 31) / 32;
       int k0 = lane * per, k1 = min(k0 + per, na);
@@ -383,7 +384,7 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
     }
   }
   __syncthreads();
-  for (int q = tid; q < nr * na; q += kThreads) {
+  for (int q = tid; q < nr * na; q += (int)blockDim.x) {
     int r = q / na, b = q % na;
     if (!((mask >> r) & 1u)) continue;
     int tgt[4];
@@ -398,7 +399,7 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
     }
   }
   __syncthreads();
-  for (int q = tid; q < nr * na; q += kThreads) {
+  for (int q = tid; q < nr * na; q += (int)blockDim.x) {
     int r = q / na, t = q % na;
     if (!((mask >> r) & 1u)) continue;
     AEnt<T>* L = ent + r * 4 * na;
@@ -623,16 +624,16 @@ struct FluxSmem {
   ff* zd_f;
   float* zq_f;     // [nang] phi^6 u^0 dOmega / dt
   double* zrow;    // [ns][ne][5] collision moment partials
-  double* wr_r;    // [kWarps][nang] f* of the warp's collision row   (aliases buf)
-  double* wr_i;    // [kWarps][nang] 1/D per warp row                 (aliases buf)
-  double* red;     // [kWarps * 2]
+  double* wr_r;    // [warps][nang] f* of the warp's collision row   (aliases buf)
+  double* wr_i;    // [warps][nang] 1/D per warp row                 (aliases buf)
+  double* red;     // [kMaxWarps * 2]
   double* tally;   // [ns][2] outflow N, E of this zone
   double* corr;    // [ns] exact-total correction of dN (mixed)
   int* corr_at;    // [ns]
   ff* dtot;        // [ns] exact total of the deposits (mixed)
-  ff* redf;        // [kWarps]
-  float* rkey;     // [kWarps]
-  int* ridx;       // [kWarps]
+  ff* redf;        // [kMaxWarps]
+  float* rkey;     // [kMaxWarps]
+  int* ridx;       // [kMaxWarps]
   unsigned long long* bar;  // mbarrier of the stencil copies
   T* buf;          // [8][ne][nang]: 4 stencil/g buffers, 4 work buffers
   Wt<T>* W;        // [6][nang]   (aliases the work buffers)
@@ -659,7 +660,7 @@ struct FluxSmem {
 };
 
 template <typename T>
-__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, FluxSmem<T>* s, unsigned char* base) {
+__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, int nw, FluxSmem<T>* s, unsigned char* base) {
   size_t o = 0;
   const int nbin = ne * nang;
 #define BT_TAKE(ptr, type, count)                              \
@@ -678,14 +679,14 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, F
   BT_TAKE(zd_f, ff, nang);
   BT_TAKE(zq_f, float, nang);
   BT_TAKE(zrow, double, (size_t)ns * ne * 5);
-  BT_TAKE(red, double, kWarps * 2);
+  BT_TAKE(red, double, kMaxWarps * 2);
   BT_TAKE(tally, double, ns * 2);
   BT_TAKE(corr, double, ns);
   BT_TAKE(corr_at, int, ns);
   BT_TAKE(dtot, ff, ns);
-  BT_TAKE(redf, ff, kWarps);
-  BT_TAKE(rkey, float, kWarps);
-  BT_TAKE(ridx, int, kWarps);
+  BT_TAKE(redf, ff, kMaxWarps);
+  BT_TAKE(rkey, float, kMaxWarps);
+  BT_TAKE(ridx, int, kMaxWarps);
   {
     // buf = 4 stencil buffers followed by 4 work buffers.  The remap weights
     // and list counters live only until the lists are built, when the work
@@ -696,7 +697,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, F
     size_t o_c = (o_work + sizeof(Wt<T>) * (size_t)6 * nang + 15) & ~size_t(15);
     size_t need_work = sizeof(T) * (size_t)4 * nbin;
     size_t need_wc = o_c + sizeof(int) * (size_t)6 * nang - o_work;
-    size_t need_col = sizeof(double) * (size_t)2 * kWarps * nang;
+    size_t need_col = sizeof(double) * (size_t)2 * nw * nang;
     size_t tot = stencil + (need_work > need_wc ? need_work : need_wc);
     if (need_col > tot) tot = need_col;
     if (s) {
@@ -704,7 +705,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, F
       s->W = reinterpret_cast<Wt<T>*>(base + o_work);
       s->cnt = reinterpret_cast<int*>(base + o_c);
       s->wr_r = reinterpret_cast<double*>(base + o_b);
-      s->wr_i = reinterpret_cast<double*>(base + o_b) + (size_t)kWarps * nang;
+      s->wr_i = reinterpret_cast<double*>(base + o_b) + (size_t)nw * nang;
     }
     o = o_b + tot;
   }
@@ -758,7 +759,7 @@ __device__ __forceinline__ double block_sum2(double v0, double v1, double* red, 
   if (lane == 0) { red[2 * w] = v0; red[2 * w + 1] = v1; }
   __syncthreads();
   double s0 = 0.0, s1 = 0.0;
-  for (int i = 0; i < kWarps; ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
+  for (int i = 0; i < ((int)blockDim.x >> 5); ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
   __syncthreads();
   out1 = s1;
   return s0;
@@ -772,7 +773,7 @@ __device__ __forceinline__ ff block_sum_ff(ff v, ff* red) {
   if (lane == 0) red[w] = v;
   __syncthreads();
   ff t = red[0];
-  for (int i = 1; i < kWarps; ++i) t = ff_add(t, red[i]);
+  for (int i = 1; i < ((int)blockDim.x >> 5); ++i) t = ff_add(t, red[i]);
   __syncthreads();
   return t;
 }
@@ -790,7 +791,7 @@ __device__ __forceinline__ int block_argmax(float key, int idx, float* rk, int* 
   __syncthreads();
   float bk = rk[0];
   int bi = ri[0];
-  for (int i = 1; i < kWarps; ++i)
+  for (int i = 1; i < ((int)blockDim.x >> 5); ++i)
     if (rk[i] > bk || (rk[i] == bk && ri[i] < bi)) { bk = rk[i]; bi = ri[i]; }
   __syncthreads();
   return bi;
@@ -804,7 +805,7 @@ __device__ __forceinline__ ff conservation_residual(const float* dep, int n, ff 
   ff part = ff{0.0f, 0.0f};
   float bk = -1.0f;
   int bi = 0x7fffffff;
-  for (int q = threadIdx.x; q < n; q += kThreads) {
+  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
     part = ff_add(part, dep[q]);
     float k = fabsf(dep[q]);
     if (k > bk) { bk = k; bi = q; }
@@ -838,19 +839,19 @@ struct AddDN {   // dN += sign * T[F]
   __device__ void operator()(int t, T acc) const { dn[t * na + b] += (typename DNT<T>::type)(sign * acc); }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_collide(Tables tb, State st, double dt) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT) : 1) k_flux_collide(Tables tb, State st, double dt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using DN = typename DNT<T>::type;
   FluxSmem<T> S;
-  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, &S, smem_raw);
+  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, &S, smem_raw);
   const int zone = blockIdx.x;
   const int a = zone % tb.n_r, b = zone / tb.n_r;
   const int NE = tb.n_e, NA = tb.n_ang, NS = tb.n_s, NPH = tb.n_ph, NMU = tb.n_mu;
   const int nbin = NE * NA;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int nch = kThreads / NA > 0 ? kThreads / NA : 1;   // row chunks
+  const int nch = NT / NA > 0 ? NT / NA : 1;   // row chunks
   const int gb = tid % NA, gc = tid / NA;                   // this thread's angle, chunk
   const bool gact = tid < nch * NA;
   const T* fin = reinterpret_cast<const T*>(st.f);
@@ -861,19 +862,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
   const bool use_tma = (rowbytes % 16u) == 0u;
   unsigned tphase = 0;               // parity of the next mbarrier phase to wait for
 
-  for (int q = tid; q < NS * nbin; q += kThreads) S.dN[q] = DN(0);
-  for (int q = tid; q < NMU; q += kThreads) S.mu[q] = (T)tb.mu[q];
-  for (int q = tid; q < NA; q += kThreads) {
+  for (int q = tid; q < NS * nbin; q += NT) S.dN[q] = DN(0);
+  for (int q = tid; q < NMU; q += NT) S.mu[q] = (T)tb.mu[q];
+  for (int q = tid; q < NA; q += NT) {
     int j = q / NPH, k = q % NPH;
     S.n0[q] = (T)tb.mu[j];
     S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
     S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
     S.dOm[q] = (T)tb.dOm[q];
   }
-  for (int q = tid; q < NE; q += kThreads) { S.dGam[q] = (T)tb.dGam[q]; S.rdGam[q] = (T)(1.0 / tb.dGam[q]); }
-  for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = (T)tb.p3[q];
-  for (int q = tid; q < NS * 2; q += kThreads) S.tally[q] = 0.0;
-  for (int q = tid; q < NS; q += kThreads) S.dtot[q] = ff{0.0f, 0.0f};
+  for (int q = tid; q < NE; q += NT) { S.dGam[q] = (T)tb.dGam[q]; S.rdGam[q] = (T)(1.0 / tb.dGam[q]); }
+  for (int q = tid; q < 2 * NE + 3; q += NT) S.p3[q] = (T)tb.p3[q];
+  for (int q = tid; q < NS * 2; q += NT) S.tally[q] = 0.0;
+  for (int q = tid; q < NS; q += NT) S.dtot[q] = ff{0.0f, 0.0f};
   if (tid == 0) mbar_init(S.bar, 1);
   const int nface = tb.slab ? 2 : kFaces;
   if (tid < nface) {
@@ -937,7 +938,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     const T Rg = (T)tb.R;
     {
       const Loc<T> Ls = LF[4];
-      for (int q = tid; q < 6 * NA; q += kThreads) {
+      for (int q = tid; q < 6 * NA; q += NT) {
         int r = q / NA, ang = q % NA;
         if (!((mask >> r) & 1u)) continue;
         int slot = r < 4 ? r : r - 3;
@@ -948,7 +949,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
         S.W[r * NA + ang] = w;
       }
       // face bins: Eulerian energy factor and normal coordinate velocity
-      for (int ang = tid; ang < NA; ang += kThreads) {
+      for (int ang = tid; ang < NA; ang += NT) {
         T n[3] = {S.n0[ang], S.n1[ang], S.n2[ang]};
         T e, p[3];
         boost_fwd(Ls, n, e, p);
@@ -984,7 +985,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     for (int s = 0; s < NS; ++s) {
       // face opacities and flux-switch weights per group [R-10, R-12b]
       if (F.type == F_INTERNAL) {
-        for (int i = tid; i < NE; i += kThreads) {
+        for (int i = tid; i < NE; i += NT) {
           size_t oP = ((size_t)s * tb.n_zone + F.z[1]) * NE + i;
           size_t oQ = ((size_t)s * tb.n_zone + F.z[2]) * NE + i;
           double kaP = st.ka[oP], kaQ = st.ka[oQ], ksP = st.ks[oP], ksQ = st.ks[oQ];
@@ -1059,7 +1060,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
         }
         __syncthreads();
         // J per group (Sherman-Morrison closed form; one warp per row)
-        for (int i = warp; i < NE; i += kWarps) {
+        for (int i = warp; i < NE; i += (NT / 32)) {
           T sr = T(0), s1 = T(0);
           const T ka = S.kaS[i];
           for (int ang = lane; ang < NA; ang += 32) {
@@ -1175,7 +1176,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
       ff part = ff{0.0f, 0.0f};
       float bk = -1.0f;
       int bi = 0x7fffffff;
-      for (int q = tid; q < nbin; q += kThreads) {
+      for (int q = tid; q < nbin; q += NT) {
         const float c = (float)dNs[q] * (float)S.dGam[q / NA];
         part = ff_add(part, two_prod((float)dNs[q], (float)S.dGam[q / NA]));
         float k = fabsf(c);
@@ -1190,7 +1191,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
       }
     }
   } else {
-    for (int s = tid; s < NS; s += kThreads) { S.corr[s] = 0.0; S.corr_at[s] = -1; }
+    for (int s = tid; s < NS; s += NT) { S.corr[s] = 0.0; S.corr_at[s] = -1; }
   }
 
   // --- implicit collision per (species, group) (Sec. 3.5) and moments (Eq. hydrosource)
@@ -1202,7 +1203,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     const double* v = st.v + 3 * zone;
     double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     double gz = 1.0 / sqrt(1.0 - v2);
-    for (int ang = tid; ang < NA; ang += kThreads) {
+    for (int ang = tid; ang < NA; ang += NT) {
       int j = ang / NPH, k = ang % NPH;
       double nv = v[0] * tb.mu[j] + (v[1] * tb.cph[k] + v[2] * tb.sph[k]) * tb.smu[j];
       double u0 = gz * (1.0 + nv);
@@ -1216,7 +1217,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     }
   }
   __syncthreads();
-  for (int row = warp; row < NS * NE; row += kWarps) {
+  for (int row = warp; row < NS * NE; row += (NT / 32)) {
     const int s = row / NE, i = row % NE;
     const size_t oz = ((size_t)s * tb.n_zone + zone) * NE + i;
     const double ka = st.ka[oz], ks = st.ks[oz], fe = st.fe[oz];
@@ -1335,7 +1336,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1) k_flux_colli
     }
   }
   __syncthreads();
-  for (int s = tid; s < NS; s += kThreads) {
+  for (int s = tid; s < NS; s += NT) {
     double m[5] = {0, 0, 0, 0, 0};
     for (int i = 0; i < NE; ++i)
       for (int c = 0; c < 5; ++c) m[c] += S.zrow[((size_t)s * NE + i) * 5 + c];
@@ -1628,34 +1629,66 @@ __global__ void k_jhk(Tables tb, State st, double* J, double* H, double* K) {
   }
 }
 
-template <typename T>
+template <typename T, int NT>
 int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) {
-  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
-  cudaError_t e = cudaFuncSetAttribute(k_flux_collide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return (int)e;
-  k_flux_collide<T><<<tb.n_zone, kThreads, sm, s>>>(tb, st, dt);
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, nullptr, nullptr);
+  k_flux_collide<T, NT><<<tb.n_zone, NT, sm, s>>>(tb, st, dt);
   return (int)cudaGetLastError();
+}
+
+template <typename T, int NT>
+int flux_occupancy_t(const Tables& tb) {
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, nullptr, nullptr);
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_flux_collide<T, NT>, NT, sm) != cudaSuccess) return 0;
+  return blocks;
 }
 
 template <typename T>
 int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
   size_t sm = remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
-  cudaError_t e = cudaFuncSetAttribute(k_time_remap<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return (int)e;
   k_time_remap<T><<<tb.n_zone, kThreads, sm, s>>>(tb, st);
   return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-size_t flux_smem_bytes(const Tables& tb, int mixed) {
-  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr)
-               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
+size_t flux_smem_bytes(const Tables& tb, int mixed, int nt) {
+  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nt / 32, nullptr, nullptr)
+               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nt / 32, nullptr, nullptr);
 }
 size_t remap_smem_bytes(const Tables& tb, int mixed) {
   return mixed ? remap_smem_layout<float>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr)
                : remap_smem_layout<double>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
 }
+// Allow the large dynamic shared-memory carve-outs once (a function
+// attribute, set outside any stream capture).
+int prepare_kernels() {
+  int dev = 0, lim = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaSuccess;
+#define BT_SET(fn) if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+  BT_SET((k_flux_collide<float, 128>));
+  BT_SET((k_flux_collide<float, 256>));
+  BT_SET((k_flux_collide<float, 512>));
+  BT_SET((k_flux_collide<double, 128>));
+  BT_SET((k_flux_collide<double, 256>));
+  BT_SET((k_flux_collide<double, 512>));
+  BT_SET((k_time_remap<float>));
+  BT_SET((k_time_remap<double>));
+#undef BT_SET
+  return (int)e;
+}
+
+int flux_occupancy(const Tables& tb, int mixed, int nt) {
+  switch (nt) {
+    case 128: return mixed ? flux_occupancy_t<float, 128>(tb) : flux_occupancy_t<double, 128>(tb);
+    case 512: return mixed ? flux_occupancy_t<float, 512>(tb) : flux_occupancy_t<double, 512>(tb);
+    default: return mixed ? flux_occupancy_t<float, 256>(tb) : flux_occupancy_t<double, 256>(tb);
+  }
+}
+
 int max_optin_smem() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -1663,9 +1696,13 @@ int max_optin_smem() {
   return v;
 }
 
-int launch_flux_collide(const Tables& tb, const State& st, double dt, int mixed, void* stream) {
+int launch_flux_collide(const Tables& tb, const State& st, double dt, int mixed, int nt, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  return mixed ? launch_flux_t<float>(tb, st, dt, s) : launch_flux_t<double>(tb, st, dt, s);
+  switch (nt) {
+    case 128: return mixed ? launch_flux_t<float, 128>(tb, st, dt, s) : launch_flux_t<double, 128>(tb, st, dt, s);
+    case 512: return mixed ? launch_flux_t<float, 512>(tb, st, dt, s) : launch_flux_t<double, 512>(tb, st, dt, s);
+    default: return mixed ? launch_flux_t<float, 256>(tb, st, dt, s) : launch_flux_t<double, 256>(tb, st, dt, s);
+  }
 }
 
 int launch_time_remap(const Tables& tb, const State& st, int mixed, void* stream) {
