@@ -129,6 +129,28 @@ FP32_PEAK_TFLOPS = GB300_SMS * GB300_FP32_LANES * 2 * GB300_SM_GHZ / 1e3
 FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one flux
+# launch from an ncu capture (profiles/k_flux_collide_*_config3.md), keyed by
+# workload, precision and launch shape, and valid only for the kernel source
+# it was taken on: a changed bt_kernels.cu reports null until re-captured.
+TRAFFIC = {
+    ("config3_cc2d_256x64x12x80x3", "mixed", 256):
+        (371.97e6, "85cb2f212c7785ccc48af3435cf2633ee70ea9baa0f04b0f2a4a6a882c4041d2"),
+    ("config3_cc2d_256x64x12x80x3", "fp64", 256):
+        (755.74e6, "85cb2f212c7785ccc48af3435cf2633ee70ea9baa0f04b0f2a4a6a882c4041d2"),
+}
+
+
+def measured_traffic(workload, precision, nt):
+    import hashlib
+    rec = TRAFFIC.get((workload, precision, nt))
+    if rec is None:
+        return None
+    src = os.path.join(ROOT, "paper_2003_02845_gb300", "csrc", "bt_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return rec[0] if sha == rec[1] else None
+
+
 def algorithmic_flops_per_bin(prob):
     """Arithmetic the method needs per zone-group-angle-species bin and step,
     counted on unique faces (3 per zone in spherical geometry, 1 in a slab):
@@ -286,7 +308,8 @@ def run_ours(args):
                 GB300_SMS, GB300_FP32_LANES, GB300_SM_GHZ, "" if mixed else " / 64 (float64)"),
             "unit": "TFLOP/s",
             "frac": achieved_tf / peak_tf,
-            "traffic": None,
+            "traffic": measured_traffic(prob.name, args.precision, t.launch_shape),
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
             "algorithmic_flops_per_bin": fpb,
             "avg_launch_ms": flux_avg_ms,
             "time_remap_avg_ms": remap_ms / max(remap_n, 1),
@@ -572,7 +595,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--autotune", action="store_true", help="pick each problem's launch shape by timing")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shape instead of timing the candidates")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

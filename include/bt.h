@@ -230,6 +230,77 @@ int bt_batch_destroy(bt_batch* b);
 int bt_weighted_totals_noalloc(const void* f, int precision, int n_s, int n_zone, int n_e, int n_ang,
                                const double* w_za, const double* w_e, double* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned remap: a small network that predicts the remap's redistribution
+ * weights (the paper has no counterpart; its remap weights are the exact
+ * trilinear ones of Sec. 3.2, which stay the judge and the fallback).
+ *
+ * Network: x (BT_SUR_NIN = 16 features) -> normalise (x - mean) * scale ->
+ * 64 -> 64 -> 64 (GELU, exact erf form) -> 27 logits -> softmax P over the
+ * offsets {-1,0,1}^3 of (energy group, mu index, Phi index), offset (de, dm,
+ * dp) at index 9 (de+1) + 3 (dm+1) + (dp+1).  Evaluated and trained on the
+ * tensor cores with bf16 operands and fp32 accumulation.
+ *
+ * Parameter block (BT_SUR_NPARAM floats, fp32): W1 [64][16], b1 [64],
+ * W2 [64][64], b2 [64], W3 [64][64], b3 [64], W4 [27][64], b4 [27],
+ * mean [16], scale [16]; W_l row-major [out][in].
+ *
+ * A bt_surrogate owns its parameters, gradient and Adam state on the device
+ * and enqueues on `stream`.  X, Y, P, grad and loss below are DEVICE pointers
+ * owned by the caller: X [n][16], Y and P [n][27] row-major fp32.  The calls
+ * synchronise and return BT_ERR_TIMEOUT if a bounded tensor-core wait gave
+ * up (the results are then invalid).
+ * ------------------------------------------------------------------------ */
+/* Training rows of the learned remap from the handle's exact remap (the
+ * emit mode of Sec. 3.2's weights).  Row i is idx[i] = (zone, kind, source
+ * angle): kind 0 is the zone's time remap from the previous to the current
+ * background (G = I); kind 1 + 6 f + r (f = 0..4: inner and outer radial,
+ * lower and upper polar -- or the periodic polar face of a column --, and the
+ * azimuthal face of the zone) is remap r of face f: r = 0..3 carries stencil
+ * cell r (zones P-1, P, Q, Q+1) into the face frame, r = 4, 5 carries the
+ * face frame into cell P, Q.  Outputs, per row:
+ *   X[i][16]  features: source direction n (0-2), source velocity (3-5),
+ *             destination velocity in the source triad (6-8), rotation
+ *             vector of the source -> destination triad rotation (9-11),
+ *             ln(alpha_src/alpha_dst) on the kick axis (12-14, zero for the
+ *             time remap), ln((phi_src/phi_dst)^2) (15);
+ *   Y[i][27]  the exact trilinear weights on the offsets {-1,0,1}^3 of
+ *             (group, mu index, Phi index), Phi offsets wrapped;
+ *   valid[i]  1 = usable, 2 = a weight lands outside the offsets (Y = 0),
+ *             0 = no such remap (absent face or cell, or idx out of range).
+ * idx, X, Y and valid are DEVICE pointers; computed in float64, stored as
+ * float32.  Needs two backgrounds set (BT_ERR_STATE otherwise).  Synchronises. */
+int bt_sur_samples(bt_handle* h, const int32_t* idx, int64_t n, float* X, float* Y, int32_t* valid);
+
+#define BT_SUR_NIN 16
+#define BT_SUR_NOUT 27
+#define BT_SUR_NPARAM 11195
+typedef struct bt_surrogate bt_surrogate;
+typedef struct {
+  int32_t epochs;  /* passes over the samples */
+  int32_t batch;   /* rows per Adam step (the last batch of a pass may be short) */
+  float lr, lr_final;   /* cosine decay from lr to lr_final over all steps */
+  float beta1, beta2, eps;
+} bt_train_cfg;
+int bt_sur_create(void* stream, bt_surrogate** out);
+int bt_sur_destroy(bt_surrogate* s);
+/* copy the BT_SUR_NPARAM parameters in (resets the Adam state) or out */
+int bt_sur_set_params(bt_surrogate* s, int mem, const float* p);
+int bt_sur_get_params(bt_surrogate* s, int mem, float* p);
+/* mean and scale = 1/standard deviation of each feature over X [n][16] */
+int bt_sur_fit_normalizer(bt_surrogate* s, const float* X, int64_t n);
+/* P = network(X) */
+int bt_sur_forward(bt_surrogate* s, const float* X, int64_t n, float* P);
+/* grad [BT_SUR_NPARAM] = gradient of the mean cross entropy
+ * -1/n sum_rows sum_o Y log P over the n rows, loss [1] = that mean
+ * (normaliser entries of grad are 0) */
+int bt_sur_grad(bt_surrogate* s, const float* X, const float* Y, int64_t n, float* grad, float* loss);
+/* Adam on the mean cross entropy, minibatches taken in order (pass
+ * shuffled samples); loss_log (HOST, [epochs] or NULL) gets each pass's mean
+ * batch loss */
+int bt_sur_train(bt_surrogate* s, const float* X, const float* Y, int64_t n, const bt_train_cfg* cfg,
+                 float* loss_log);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,14 @@ class BtConfig(C.Structure):
     ]
 
 
+class BtTrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+SUR_NIN, SUR_NOUT, SUR_NPARAM = 16, 27, 11195
+
+
 class BtError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("bt error %d: %s" % (code, msg))
@@ -78,6 +86,14 @@ def lib():
         L.bt_batch_destroy.argtypes = [vp]
         L.bt_profile.argtypes = [vp, i32]
         L.bt_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.bt_sur_create.argtypes = [vp, C.POINTER(vp)]
+        L.bt_sur_destroy.argtypes = [vp]
+        L.bt_sur_set_params.argtypes = [vp, i32, vp]
+        L.bt_sur_get_params.argtypes = [vp, i32, vp]
+        L.bt_sur_fit_normalizer.argtypes = [vp, vp, C.c_int64]
+        L.bt_sur_forward.argtypes = [vp, vp, C.c_int64, vp]
+        L.bt_sur_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
+        L.bt_sur_train.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(BtTrainCfg), vp]
         _lib = L
     return _lib
 
@@ -342,3 +358,61 @@ def run(prob, precision="fp64", n_steps=None, dt=None, cfl=None):
             t.set_background(prob.backgrounds[(k + 1) % 2])
         t.step(dt)
     return t, dt
+
+
+class Surrogate:
+    """The learned remap's network (bt_sur_* in include/bt.h).  Inputs and
+    outputs are contiguous float32 CUDA tensors; parameters go in and out as
+    host numpy float32 vectors of SUR_NPARAM entries."""
+
+    def __init__(self, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib().bt_sur_create(self.stream.cuda_stream, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bt_sur_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        assert p.size == SUR_NPARAM
+        _check(lib().bt_sur_set_params(self.h, BT_MEM_HOST, p.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(SUR_NPARAM, dtype=np.float32)
+        _check(lib().bt_sur_get_params(self.h, BT_MEM_HOST, p.ctypes.data))
+        return p
+
+    def fit_normalizer(self, X):
+        _check(lib().bt_sur_fit_normalizer(self.h, X.data_ptr(), X.shape[0]))
+
+    def forward(self, X, out=None):
+        import torch
+        n = X.shape[0]
+        if out is None:
+            out = torch.empty((n, SUR_NOUT), dtype=torch.float32, device=X.device)
+        _check(lib().bt_sur_forward(self.h, X.data_ptr(), n, out.data_ptr()))
+        return out
+
+    def grad(self, X, Y):
+        import torch
+        g = torch.empty(SUR_NPARAM, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib().bt_sur_grad(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], g.data_ptr(), loss.data_ptr()))
+        return g, float(loss.item())
+
+    def train(self, X, Y, epochs, batch=4096, lr=2e-3, lr_final=5e-5, beta1=0.9, beta2=0.999, eps=1e-8):
+        cfg = BtTrainCfg(int(epochs), int(batch), lr, lr_final, beta1, beta2, eps)
+        log = np.zeros(int(epochs), dtype=np.float32)
+        _check(lib().bt_sur_train(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], C.byref(cfg), log.ctypes.data))
+        return log

@@ -18,6 +18,7 @@
 
 #include "bt.h"
 #include "bt_internal.h"
+#include "bt_mlp.h"
 
 namespace {
 
@@ -151,6 +152,7 @@ struct bt_handle {
   double* qye;
   double* tmp;        // small device scratch (rates, totals)
   bool has_bg, remap_pending;
+  int n_bg = 0;        // backgrounds set so far (capped at 2)
   int64_t launches;
   size_t nzone, nbin_total, fbytes;
   int nt;              // block size of the flux kernel (autotuned)
@@ -549,6 +551,7 @@ int bt_set_background(bt_handle* h, int mem, const double* rho, const double* T,
   if (h->has_bg) h->remap_pending = true;
   h->cur = nxt;
   h->has_bg = true;
+  if (h->n_bg < 2) ++h->n_bg;
   return BT_OK;
 }
 
@@ -754,6 +757,18 @@ int bt_jhk(bt_handle* h, int mem, double* J, double* H, double* K) {
 
 int64_t bt_launch_count(const bt_handle* h) { return h ? h->launches : 0; }
 
+int bt_sur_samples(bt_handle* h, const int32_t* idx, int64_t n, float* X, float* Y, int32_t* valid) {
+  if (!h || (n > 0 && (!idx || !X || !Y || !valid)) || n < 0) return fail(BT_ERR_ARG, "NULL or n < 0");
+  if (h->n_bg < 2) return fail(BT_ERR_STATE, "bt_sur_samples needs a previous and a current background");
+  bind_state(h);
+  int e = bt::launch_sur_samples(h->tb, h->st, idx, (long long)n, X, Y, valid, h->stream);
+  h->launches += n > 0 ? 1 : 0;
+  if (e) return cuda_fail((cudaError_t)e, "bt_sur_samples");
+  cudaError_t ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "bt_sur_samples");
+  return BT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Batched step: many independent problems advanced by one graph launch.
 // ---------------------------------------------------------------------------
@@ -906,6 +921,204 @@ int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launche
   }
   *total_ms = tot;
   *launches = n;
+  return BT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The learned remap's network (bt_sur_*): parameters, normaliser, Adam state.
+// ---------------------------------------------------------------------------
+struct bt_surrogate {
+  cudaStream_t stream = nullptr;
+  float* prm = nullptr;    // [kNParam] fp32 master parameters
+  float* grad = nullptr;   // [kNParam]
+  float* m = nullptr;      // Adam moments [kNTrain]
+  float* v = nullptr;
+  float* loss = nullptr;   // [1] loss of the last batch
+  int* flag = nullptr;     // [4] device-side error flags
+  double* stats = nullptr; // [32] feature sums for the normaliser
+  int n_sm = 0;
+  int64_t adam_t = 0;      // Adam step count
+};
+
+namespace {
+
+std::mutex g_mlp_mutex;
+bool g_mlp_prepared[64];
+
+int sur_sync(bt_surrogate* s, const char* what) {
+  int fl[4];
+  cudaError_t e = cudaMemcpyAsync(fl, s->flag, 16, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  if (fl[1]) return fail(BT_ERR_TIMEOUT, std::string(what) + ": a tensor-core wait gave up");
+  return BT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bt_sur_create(void* stream, bt_surrogate** out) {
+  if (!out) return fail(BT_ERR_ARG, "NULL");
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  {
+    std::lock_guard<std::mutex> lock(g_mlp_mutex);
+    if (dev >= 0 && dev < 64 && !g_mlp_prepared[dev]) {
+      int rc = bt::mlp::prepare();
+      if (rc) return cuda_fail((cudaError_t)rc, "network kernels: shared memory opt-in");
+      g_mlp_prepared[dev] = true;
+    }
+  }
+  bt_surrogate* s = new bt_surrogate();
+  s->stream = (cudaStream_t)stream;
+  cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t np = bt::mlp::kNParam, nt = bt::mlp::kNTrain;
+  e = cudaMalloc(&s->prm, 4 * np);
+  if (e == cudaSuccess) e = cudaMalloc(&s->grad, 4 * np);
+  if (e == cudaSuccess) e = cudaMalloc(&s->m, 4 * nt);
+  if (e == cudaSuccess) e = cudaMalloc(&s->v, 4 * nt);
+  if (e == cudaSuccess) e = cudaMalloc(&s->loss, 4 * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&s->flag, 16);
+  if (e == cudaSuccess) e = cudaMalloc(&s->stats, 8 * 32);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->prm, 0, 4 * np, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, 4 * nt, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, 4 * nt, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->flag, 0, 16, s->stream);
+  if (e == cudaSuccess) {
+    // identity normaliser until bt_sur_fit_normalizer or bt_sur_set_params
+    std::vector<float> one(bt::mlp::kIn, 1.0f);
+    e = cudaMemcpyAsync(s->prm + bt::mlp::oScale, one.data(), 4 * bt::mlp::kIn, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  if (e != cudaSuccess) {
+    bt_sur_destroy(s);
+    return cuda_fail(e, "bt_sur_create");
+  }
+  *out = s;
+  return BT_OK;
+}
+
+int bt_sur_destroy(bt_surrogate* s) {
+  if (!s) return BT_OK;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  cudaFree(s->prm);
+  cudaFree(s->grad);
+  cudaFree(s->m);
+  cudaFree(s->v);
+  cudaFree(s->loss);
+  cudaFree(s->flag);
+  cudaFree(s->stats);
+  delete s;
+  return BT_OK;
+}
+
+int bt_sur_set_params(bt_surrogate* s, int mem, const float* p) {
+  if (!s || !p) return fail(BT_ERR_ARG, "NULL");
+  cudaError_t e = cudaMemcpyAsync(s->prm, p, 4 * (size_t)bt::mlp::kNParam,
+                                  mem == BT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, 4 * (size_t)bt::mlp::kNTrain, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, 4 * (size_t)bt::mlp::kNTrain, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_set_params");
+  s->adam_t = 0;
+  return BT_OK;
+}
+
+int bt_sur_get_params(bt_surrogate* s, int mem, float* p) {
+  if (!s || !p) return fail(BT_ERR_ARG, "NULL");
+  cudaError_t e = cudaMemcpyAsync(p, s->prm, 4 * (size_t)bt::mlp::kNParam,
+                                  mem == BT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_get_params");
+  return BT_OK;
+}
+
+int bt_sur_fit_normalizer(bt_surrogate* s, const float* X, int64_t n) {
+  if (!s || !X || n < 2) return fail(BT_ERR_ARG, "NULL or n < 2");
+  cudaError_t e = cudaMemsetAsync(s->stats, 0, 8 * 32, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_fit_normalizer");
+  int rc = bt::mlp::launch_feat_stats(X, n, s->stats, s->stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "feature statistics");
+  double acc[32];
+  e = cudaMemcpyAsync(acc, s->stats, 8 * 32, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_fit_normalizer");
+  float ms[32];
+  for (int i = 0; i < 16; ++i) {
+    const double mean = acc[i] / (double)n;
+    const double var = std::max(acc[16 + i] / (double)n - mean * mean, 0.0);
+    const double sd = std::sqrt(var);
+    ms[i] = (float)mean;
+    ms[16 + i] = (float)(sd > 1e-12 * (1.0 + std::fabs(mean)) ? 1.0 / sd : 1.0);
+  }
+  e = cudaMemcpyAsync(s->prm + bt::mlp::oMean, ms, 4 * 32, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_fit_normalizer");
+  return BT_OK;
+}
+
+int bt_sur_forward(bt_surrogate* s, const float* X, int64_t n, float* P) {
+  if (!s || (n > 0 && (!X || !P)) || n < 0) return fail(BT_ERR_ARG, "NULL or n < 0");
+  int rc = bt::mlp::launch_forward(s->prm, X, n, P, s->flag, 4 * s->n_sm, s->stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "network forward");
+  return sur_sync(s, "bt_sur_forward");
+}
+
+int bt_sur_grad(bt_surrogate* s, const float* X, const float* Y, int64_t n, float* grad, float* loss) {
+  if (!s || !X || !Y || !grad || !loss || n < 1) return fail(BT_ERR_ARG, "NULL or n < 1");
+  cudaError_t e = cudaMemsetAsync(grad, 0, 4 * (size_t)bt::mlp::kNParam, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, 4, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_grad");
+  int rc = bt::mlp::launch_grad(s->prm, X, Y, n, 1.0f / (float)n, grad, loss, s->flag, s->n_sm, s->stream);
+  if (rc) return cuda_fail((cudaError_t)rc, "network gradient");
+  return sur_sync(s, "bt_sur_grad");
+}
+
+int bt_sur_train(bt_surrogate* s, const float* X, const float* Y, int64_t n, const bt_train_cfg* cfg,
+                 float* loss_log) {
+  if (!s || !X || !Y || !cfg || n < 1) return fail(BT_ERR_ARG, "NULL or n < 1");
+  if (cfg->epochs < 1 || cfg->batch < 1) return fail(BT_ERR_ARG, "epochs and batch must be >= 1");
+  const int64_t batch = std::min<int64_t>(cfg->batch, n);
+  const int64_t steps = (n + batch - 1) / batch;
+  const int64_t total = steps * cfg->epochs;
+  float* eloss = nullptr;
+  cudaError_t e = cudaMallocAsync(&eloss, 4 * (size_t)cfg->epochs, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(eloss, 0, 4 * (size_t)cfg->epochs, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_train");
+  int64_t k = 0;
+  for (int ep = 0; ep < cfg->epochs; ++ep) {
+    for (int64_t b = 0; b < steps; ++b, ++k) {
+      const int64_t b0 = b * batch, nb = std::min(batch, n - b0);
+      e = cudaMemsetAsync(s->grad, 0, 4 * (size_t)bt::mlp::kNParam, s->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(s->loss, 0, 4, s->stream);
+      if (e != cudaSuccess) { cudaFreeAsync(eloss, s->stream); return cuda_fail(e, "bt_sur_train"); }
+      int rc = bt::mlp::launch_grad(s->prm, X + b0 * bt::mlp::kIn, Y + b0 * bt::mlp::kOut, nb, 1.0f / (float)nb,
+                                    s->grad, s->loss, s->flag, s->n_sm, s->stream);
+      // cosine decay from lr to lr_final over the run
+      const double c = 0.5 * (1.0 + std::cos(kPi * (double)k / (double)std::max<int64_t>(total - 1, 1)));
+      const float lr = (float)(cfg->lr_final + (cfg->lr - cfg->lr_final) * c);
+      ++s->adam_t;
+      const float bc1 = (float)(1.0 - std::pow((double)cfg->beta1, (double)s->adam_t));
+      const float bc2 = (float)(1.0 - std::pow((double)cfg->beta2, (double)s->adam_t));
+      if (!rc)
+        rc = bt::mlp::launch_adam(s->prm, s->grad, s->m, s->v, lr, cfg->beta1, cfg->beta2, cfg->eps, bc1, bc2,
+                                  s->loss, eloss + ep, s->stream);
+      if (rc) { cudaFreeAsync(eloss, s->stream); return cuda_fail((cudaError_t)rc, "network training"); }
+    }
+  }
+  std::vector<float> lg(cfg->epochs);
+  e = cudaMemcpyAsync(lg.data(), eloss, 4 * (size_t)cfg->epochs, cudaMemcpyDeviceToHost, s->stream);
+  cudaFreeAsync(eloss, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_sur_train");
+  int rc = sur_sync(s, "bt_sur_train");
+  if (rc != BT_OK) return rc;
+  if (loss_log)
+    for (int ep = 0; ep < cfg->epochs; ++ep) loss_log[ep] = lg[ep] / (float)steps;
   return BT_OK;
 }
 

@@ -84,6 +84,10 @@ int launch_accumulate_outflow(const Tables& T, const State& S, void* stream);
 int launch_max_rate(const Tables& T, const State& S, double* d_rate /*[1]*/, void* stream);
 int launch_jhk(const Tables& T, const State& S, int mixed, double* J, double* H, double* K, void* stream);
 int launch_check_finite(const Tables& T, const State& S, int mixed, void* stream);
+// learned remap: features X [n][16], exact targets Y [n][27] and validity of
+// the rows idx [n][3] = (zone, kind, source angle)
+int launch_sur_samples(const Tables& T, const State& S, const int* idx, long long n, float* X, float* Y, int* valid,
+                       void* stream);
 size_t flux_smem_bytes(const Tables& T, int mixed, int nt);
 size_t remap_smem_bytes(const Tables& T, int mixed);
 int max_optin_smem();

@@ -139,10 +139,8 @@ __device__ __forceinline__ float exp_t(float x) { return expf(x); }
 // -> rotation G (src triad -> dst triad; transposed if gT) -> comoving(dst),
 // then the trilinear weights (Sec. 3.2, Eq. interpolation).
 template <typename T>
-__device__ void chain_weights(const Tables& tb, const T* s_mu, const T* n0, const T* n1, const T* n2,
-                              const Loc<T>& X, const Loc<T>& Y, const T* G, int gT, int axis, int ang, T R,
-                              Wt<T>& w) {
-  T n[3] = {n0[ang], n1[ang], n2[ang]};
+__device__ void chain_weights_dir(const Tables& tb, const T* s_mu, const T* n, const Loc<T>& X, const Loc<T>& Y,
+                                  const T* G, int gT, int axis, T R, Wt<T>& w) {
   T e, p[3];
   boost_fwd(X, n, e, p);
   T a = X.al / Y.al;
@@ -195,6 +193,14 @@ __device__ void chain_weights(const Tables& tb, const T* s_mu, const T* n0, cons
   }
   w.wmu = wm; w.wph = wp; w.we = we;
   w.jL = (short)jL; w.kL = (short)kL; w.m = (short)m; w.pad = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void chain_weights(const Tables& tb, const T* s_mu, const T* n0, const T* n1, const T* n2,
+                                              const Loc<T>& X, const Loc<T>& Y, const T* G, int gT, int axis, int ang,
+                                              T R, Wt<T>& w) {
+  const T n[3] = {n0[ang], n1[ang], n2[ang]};
+  chain_weights_dir(tb, s_mu, n, X, Y, G, gT, axis, R, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -1629,6 +1635,144 @@ __global__ void k_jhk(Tables tb, State st, double* J, double* H, double* K) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Learned remap: the rows it predicts, their input features and the exact
+// targets.  A row is (zone, kind, source angle).  kind 0 is the zone's time
+// remap (previous -> current background, Sec. 3.2 with G = I); kind
+// 1 + 6 fidx + r is remap r of the zone's face fidx (r < 4: stencil cell r ->
+// face, r = 4, 5: face -> cell 1, 2; Sec. 3.3).
+// ---------------------------------------------------------------------------
+constexpr int kSurKinds = 1 + 6 * kFaces;
+
+struct RemapRow {
+  const double* vX;
+  const double* vY;
+  double alX, alY, cfX, cfY;
+  const double* G;   // rotation passed to the chain (nullptr: none)
+  int gT;            // chain applies G transposed
+  int axis;
+};
+
+// false if the row's remap does not exist (no face, zero area, absent cell)
+__device__ bool sur_row(const Tables& tb, const State& st, int zone, int kind, FaceDesc& F, RemapRow& R) {
+  if (kind == 0) {
+    R.vX = st.v_old + 3 * zone; R.alX = st.al_old[zone]; R.cfX = st.cf_old[zone];
+    R.vY = st.v + 3 * zone; R.alY = st.al[zone]; R.cfY = st.cf[zone];
+    R.G = nullptr; R.gT = 0; R.axis = AX_TIME;
+    return true;
+  }
+  const int fidx = (kind - 1) / 6, r = (kind - 1) % 6;
+  if (!make_face(tb, st, zone % tb.n_r, zone / tb.n_r, fidx, F)) return false;
+  const int slot = r < 4 ? r : r - 3;
+  const int z = F.z[slot];
+  if (z < 0) return false;
+  R.G = F.G[slot];
+  R.axis = F.axis;
+  if (r < 4) {
+    R.vX = st.v + 3 * z; R.alX = st.al[z]; R.cfX = st.cf[z];
+    R.vY = F.v; R.alY = F.al; R.cfY = F.cf;
+    R.gT = 0;
+  } else {
+    R.vX = F.v; R.alX = F.al; R.cfX = F.cf;
+    R.vY = st.v + 3 * z; R.alY = st.al[z]; R.cfY = st.cf[z];
+    R.gT = 1;
+  }
+  return true;
+}
+
+// The 16 inputs of the network for row (R, source angle ang):
+//  0-2   source direction n in the source triad
+//  3-5   source fluid velocity (source triad)
+//  6-8   destination fluid velocity expressed in the source triad, Gc^T v_Y
+//  9-11  rotation vector of Gc (source -> destination triad), the
+//        antisymmetric part (Gc - Gc^T)/2 as a vector
+//  12-14 ln(alpha_X / alpha_Y) along the kick axis (zero for the time remap)
+//  15    ln((phi_X / phi_Y)^2)
+__device__ void sur_features(const Tables& tb, const RemapRow& R, int ang, double* f) {
+  const int j = ang / tb.n_ph, k = ang % tb.n_ph;
+  f[0] = tb.mu[j];
+  f[1] = tb.smu[j] * tb.cph[k];
+  f[2] = tb.smu[j] * tb.sph[k];
+  double Gc[9];
+  for (int m = 0; m < 3; ++m)
+    for (int c = 0; c < 3; ++c)
+      Gc[3 * m + c] = R.G ? (R.gT ? R.G[3 * c + m] : R.G[3 * m + c]) : (m == c ? 1.0 : 0.0);
+  for (int c = 0; c < 3; ++c) {
+    f[3 + c] = R.vX[c];
+    f[6 + c] = Gc[c] * R.vY[0] + Gc[3 + c] * R.vY[1] + Gc[6 + c] * R.vY[2];
+  }
+  f[9] = 0.5 * (Gc[7] - Gc[5]);
+  f[10] = 0.5 * (Gc[2] - Gc[6]);
+  f[11] = 0.5 * (Gc[3] - Gc[1]);
+  f[12] = f[13] = f[14] = 0.0;
+  if (R.axis < 3) f[12 + R.axis] = log(R.alX / R.alY);
+  f[15] = 2.0 * log(R.cfX / R.cfY);
+}
+
+// offset of a Phi index difference, wrapped to the nearest image
+__device__ __forceinline__ int phi_offset(int d, int nph) {
+  if (nph >= 3) {
+    if (2 * d >= nph) d -= nph;
+    else if (2 * d < -nph) d += nph;
+  }
+  return d;
+}
+
+// exact trilinear weights of row (R, ang) on the 27 offsets; false if a
+// nonzero weight falls outside {-1, 0, 1}^3
+__device__ bool sur_targets(const Tables& tb, const Wt<double>& w, int ang, double* y) {
+  for (int q = 0; q < 27; ++q) y[q] = 0.0;
+  const int j = ang / tb.n_ph, k = ang % tb.n_ph;
+  const int jR = tb.n_mu >= 2 ? w.jL + 1 : w.jL;
+  const int kR = tb.n_ph >= 2 ? (w.kL + 1) % tb.n_ph : w.kL;
+  bool rep = true;
+  for (int ie = 0; ie < 2; ++ie) {
+    const double we = ie ? w.we : 1.0 - w.we;
+    const int de = w.m + ie;
+    for (int ij = 0; ij < 2; ++ij) {
+      const double wm = ij ? w.wmu : 1.0 - w.wmu;
+      const int dm = (ij ? jR : w.jL) - j;
+      for (int ik = 0; ik < 2; ++ik) {
+        const double wp = ik ? w.wph : 1.0 - w.wph;
+        const int dp = phi_offset((ik ? kR : w.kL) - k, tb.n_ph);
+        const double c = we * wm * wp;
+        if (c == 0.0) continue;
+        if (de < -1 || de > 1 || dm < -1 || dm > 1 || dp < -1 || dp > 1) { rep = false; continue; }
+        y[9 * (de + 1) + 3 * (dm + 1) + (dp + 1)] += c;
+      }
+    }
+  }
+  if (!rep)
+    for (int q = 0; q < 27; ++q) y[q] = 0.0;
+  return rep;
+}
+
+__global__ void k_sur_samples(Tables tb, State st, const int* idx, long long n, float* X, float* Y, int* valid) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int zone = idx[3 * i], kind = idx[3 * i + 1], ang = idx[3 * i + 2];
+    double f[16], y[27];
+    for (int q = 0; q < 16; ++q) f[q] = 0.0;
+    for (int q = 0; q < 27; ++q) y[q] = 0.0;
+    int v = 0;
+    FaceDesc F;
+    RemapRow R;
+    if (zone >= 0 && zone < tb.n_zone && kind >= 0 && kind < kSurKinds && ang >= 0 && ang < tb.n_ang &&
+        sur_row(tb, st, zone, kind, F, R)) {
+      sur_features(tb, R, ang, f);
+      Loc<double> LX, LY;
+      make_loc(LX, R.vX, R.alX, R.cfX);
+      make_loc(LY, R.vY, R.alY, R.cfY);
+      const double n3[3] = {f[0], f[1], f[2]};
+      Wt<double> w;
+      chain_weights_dir<double>(tb, tb.mu, n3, LX, LY, R.G, R.gT, R.axis, tb.R, w);
+      v = sur_targets(tb, w, ang, y) ? 1 : 2;
+    }
+    for (int q = 0; q < 16; ++q) X[16 * i + q] = (float)f[q];
+    for (int q = 0; q < 27; ++q) Y[27 * i + q] = (float)y[q];
+    valid[i] = v;
+  }
+}
+
 template <typename T, int NT>
 int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) {
   size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, nullptr, nullptr);
@@ -1743,5 +1887,14 @@ int launch_jhk(const Tables& tb, const State& st, int mixed, double* J, double* 
 }
 
 int launch_check_finite(const Tables&, const State&, int, void*) { return 0; }
+
+int launch_sur_samples(const Tables& tb, const State& st, const int* idx, long long n, float* X, float* Y, int* valid,
+                       void* stream) {
+  if (n <= 0) return 0;
+  long long blocks = (n + 127) / 128;
+  if (blocks > 8192) blocks = 8192;
+  k_sur_samples<<<(int)blocks, 128, 0, (cudaStream_t)stream>>>(tb, st, idx, n, X, Y, valid);
+  return (int)cudaGetLastError();
+}
 
 }  // namespace bt

@@ -1,0 +1,107 @@
+"""The learned remap's network on the tensor cores against the CPU float64
+reference (oracle/mlp.py): forward pass, gradient, and training."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2003_02845_gb300 import build, bt
+    build.build()
+    return bt
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    q = mlp.unpack(mlp.init_params(seed))
+    for l in (1, 2, 3):
+        q["b%d" % l][:] = rng.normal(0, 0.2, 64)
+    q["b4"][:] = rng.normal(0, 0.2, 27)
+    q["mean"][:] = rng.normal(0, 0.2, 16)
+    q["scale"][:] = rng.uniform(0.5, 1.5, 16)
+    # the device keeps float32 parameters
+    return mlp.pack(q).astype(np.float32).astype(np.float64)
+
+
+def _inputs(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, (n, 16)).astype(np.float32)
+    Y = rng.dirichlet(np.full(27, 0.3), n).astype(np.float32)
+    return X, Y
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 4099])
+def test_forward_matches_cpu(gpu, n):
+    import torch
+    p = _params(1)
+    X, _ = _inputs(2, n)
+    s = gpu.Surrogate()
+    s.set_params(p)
+    assert np.array_equal(s.get_params(), p.astype(np.float32))
+    P = s.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    assert np.allclose(P.sum(axis=1), 1.0, atol=1e-5)
+    # same operand rounding as the tensor cores (bf16), float64 sums: only the
+    # order of the float32 sums and an occasional bf16 rounding flip differ
+    Pe = mlp.forward(p, X.astype(np.float64), operand_round=mlp.bf16)
+    assert np.abs(P - Pe).max() < 2e-3
+    assert np.abs(P - Pe).mean() < 2e-5
+    # against the plain float64 network: the bf16 operand error
+    P64 = mlp.forward(p, X.astype(np.float64))
+    assert np.abs(P - P64).max() < 3e-2
+
+
+def test_gradient_matches_cpu(gpu):
+    import torch
+    p = _params(3)
+    X, Y = _inputs(4, 3000)
+    s = gpu.Surrogate()
+    s.set_params(p)
+    g, loss = s.grad(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    L, gc = mlp.loss_and_grad(p, X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss - L) < 2e-3 * L
+    assert not np.any(g[mlp.N_PARAM - 32:])        # normaliser not trained
+    # block by block: relative error of the gradient vector and its direction
+    o = 0
+    for name, shape in mlp.SHAPES:
+        k = int(np.prod(shape))
+        if name in ("mean", "scale"):
+            break
+        a, b = g[o:o + k], gc[o:o + k]
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert rel < 3e-2 and cos > 0.999, (name, rel, cos)
+        o += k
+
+
+def test_training_reduces_loss(gpu):
+    import torch
+    # targets from a fixed smooth map of the inputs (a softmax of a random
+    # linear map), which the network can represent
+    rng = np.random.default_rng(5)
+    n = 32768
+    X = rng.normal(0, 1, (n, 16)).astype(np.float32)
+    A = rng.normal(0, 0.7, (16, 27))
+    Y = mlp.softmax(X.astype(np.float64) @ A).astype(np.float32)
+    s = gpu.Surrogate()
+    s.set_params(mlp.init_params(6).astype(np.float32))
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    s.fit_normalizer(Xd)
+    q = mlp.unpack(s.get_params().astype(np.float64))
+    assert np.allclose(q["mean"], X.mean(axis=0), atol=1e-4)
+    assert np.allclose(q["scale"], 1.0 / X.std(axis=0), rtol=1e-3)
+    _, L0 = s.grad(Xd, Yd)
+    log = s.train(Xd, Yd, epochs=8, batch=1024, lr=3e-3, lr_final=1e-4)
+    _, L1 = s.grad(Xd, Yd)
+    ent = -(Y * np.log(np.maximum(Y, 1e-30))).sum(axis=1).mean()   # the loss floor
+    assert np.all(np.isfinite(log))
+    assert log[-1] < log[0]
+    # the excess over the entropy floor shrinks at least tenfold
+    assert L1 - ent < 0.1 * (L0 - ent), (L0, L1, ent)
