@@ -324,12 +324,107 @@ def run_ours(args):
         res["vs_fp64_gpu"] = {"value": units_per_step / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                               "speedup": ms64 / ms,
                               "what": "the same step in plain FP64 on this GPU (same kernels, T = double)"}
+    if mixed and args.accuracy_steps > 0:
+        f64 = run_steps(prob, dev, "fp64", args.accuracy_steps)
+        res["accuracy"] = {"steps": args.accuracy_steps,
+                           "what": "rel-L1 of f against the plain FP64 GPU path (which matches the FP64 oracle to "
+                                   "1e-12) after the given steps, same backgrounds and dt",
+                           "mixed_rel_l1": rel_l1(run_steps(prob, dev, "mixed", args.accuracy_steps), f64)}
+        if args.learned_remap:
+            try:
+                res["learned_remap"] = learned_remap_block(prob, dev, args, ms, f64)
+            except Exception as e:   # report, do not lose the line
+                res["learned_remap"] = {"error": repr(e)}
+        del f64
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def rel_l1(a, b):
+    return float((a.double() - b.double()).abs().sum() / b.double().abs().sum())
+
+
+def run_steps(prob, dev, precision, steps, sur=None, tol=0.0):
+    """f (device tensor) after `steps` steps from f0 with the backgrounds
+    alternating as in the timed run, dt from the Courant limit of B0."""
+    import torch
+    from paper_2003_02845_gb300 import bt
+    stream = torch.cuda.Stream()
+    t = bt.Transport(prob, precision, stream=stream)
+    if sur is not None:
+        t.set_surrogate(sur, tol)
+    t.set_background(prob.backgrounds[0])
+    t.set_f(prob.f0)
+    dt = t.max_dt(prob.cfl)
+    for k in range(steps):
+        t.set_background_device(*dev[(k + 1) % 2])
+        t.step(dt)
+    f = torch.empty(prob.f0.shape, dtype=torch.float32 if precision == "mixed" else torch.float64, device="cuda")
+    t.get_f(out=f)
+    stats = t.sur_stats() if sur is not None else None
+    t.close()
+    return (f, stats) if sur is not None else f
+
+
+def learned_remap_block(prob, dev, args, ms_exact, f64):
+    """Train the network on rows of the exact remap from 16 seeded background
+    pairs (the workload's own backgrounds are held out), then time the step
+    with it and measure its error at a few trip tolerances."""
+    import torch
+    from paper_2003_02845_gb300 import bt, learned_remap as LR, workloads as W
+    t0 = time.perf_counter()
+    pairs = [W.config4_backgrounds(k) for k in range(16)]
+    X, Y = LR.training_set(prob, pairs, args.sur_samples, seed=777)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net, log = LR.train(X, Y, epochs=args.sur_epochs, batch=4096)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    n_rows = int(X.shape[0])
+    del X, Y
+    out = {"samples": n_rows, "epochs": args.sur_epochs, "batch": 4096,
+           "loss_per_epoch": [float(x) for x in log],
+           "data_seconds": t1 - t0, "train_seconds": t2 - t1, "runs": []}
+    for tol in args.sur_tols:
+        stream = torch.cuda.Stream()
+        t = bt.Transport(prob, "mixed", stream=stream)
+        net_s = net
+        t.set_surrogate(net_s, tol)
+        t.set_background(prob.backgrounds[0])
+        t.set_f(prob.f0)
+        dt = t.max_dt(prob.cfl)
+        for k in range(3):
+            t.set_background_device(*dev[(k + 1) % 2])
+            t.step(dt)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.steps):
+            t.set_background_device(*dev[(k + 4) % 2])
+            t.step(dt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_sur = ev0.elapsed_time(ev1) / args.steps
+        t.profile(True)
+        for k in range(3):
+            t.set_background_device(*dev[(k + 1) % 2])
+            t.step(dt)
+        tab_ms, tab_n = t.profile_read(bt.K_SUR_TABLE)
+        t.profile(False)
+        t.close()
+        fs, (n_eval, n_trip) = run_steps(prob, dev, "mixed", args.accuracy_steps, sur=net_s, tol=tol)
+        out["runs"].append({"tol_bins": tol, "ms_per_step": ms_sur, "value": prob.n_bins / (ms_sur * 1e-3),
+                            "speed_vs_exact_mixed": ms_exact / ms_sur,
+                            "table_kernel_ms": tab_ms / max(tab_n, 1),
+                            "trip_fraction": n_trip / max(n_eval, 1),
+                            "rel_l1_vs_fp64": rel_l1(fs, f64)})
+        del fs
+    net.close()
+    return out
 
 
 def time_fp64_path(prob, dev, steps=5, warmup=3):
@@ -595,6 +690,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--accuracy-steps", type=int, default=100,
+                    help="steps of the accuracy comparison against the FP64 path (0: skip)")
+    ap.add_argument("--no-learned-remap", dest="learned_remap", action="store_false")
+    ap.add_argument("--sur-samples", type=int, default=2_000_000)
+    ap.add_argument("--sur-epochs", type=int, default=10)
+    ap.add_argument("--sur-tols", type=float, nargs="+", default=[0.01, 0.05, 0.25])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing the candidates")
     args = ap.parse_args()

@@ -166,8 +166,9 @@ int64_t bt_launch_count(const bt_handle* h);
  * every launch of bt_step while enabled (enable = 1), for measurement.
  * bt_profile(h, 1) also clears the records.  bt_profile_read synchronises
  * the stream and returns, for kernel id BT_K_TIME_REMAP / BT_K_FLUX /
- * BT_K_OUTFLOW, the summed duration in ms and the number of launches. */
-enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2 };
+ * BT_K_OUTFLOW / BT_K_SUR_TABLE (the learned remap's table), the summed
+ * duration in ms and the number of launches. */
+enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2, BT_K_SUR_TABLE = 3 };
 int bt_profile(bt_handle* h, int enable);
 int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launches);
 
@@ -300,6 +301,22 @@ int bt_sur_grad(bt_surrogate* s, const float* X, const float* Y, int64_t n, floa
  * batch loss */
 int bt_sur_train(bt_surrogate* s, const float* X, const float* Y, int64_t n, const bt_train_cfg* cfg,
                  float* loss_log);
+
+/* Use the network for the remap weights of every bt_step of h (mixed
+ * precision only; s = NULL returns to the exact weights).  Each step first
+ * evaluates the network on all of the step's remap rows -- the time remap
+ * when the background changed, and the six remaps of every face of every
+ * zone --, takes each predicted distribution's mean offset per axis as the
+ * trilinear bracket and weight of that axis, and compares it with the exact
+ * weights of Sec. 3.2: a row whose mean offset differs by tol (in bins) or
+ * more on any axis "trips" and uses the exact weights.  tol = 0 trips every
+ * row and reproduces the exact mixed-precision step bit for bit.  Weights
+ * sum to one per axis either way, so number is conserved.  s must stay
+ * alive while set and share h's stream.  Allocates the weight table
+ * (n_zone x 31 x n_ang rows of 20 bytes) on first use. */
+int bt_set_surrogate(bt_handle* h, bt_surrogate* s, double tol);
+/* cumulative rows evaluated by the network and rows that tripped */
+int bt_sur_stats(bt_handle* h, int64_t* n_eval, int64_t* n_trip);
 
 #ifdef __cplusplus
 }

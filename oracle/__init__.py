@@ -78,6 +78,9 @@ def lib():
         L.orc_face_area_ph.argtypes = [d, d, d, d, d]
         L.orc_cell_volume.restype = d
         L.orc_cell_volume.argtypes = [d, d, d, d, d]
+        L.orc_sur_sample.restype = i
+        L.orc_sur_sample.argtypes = [p, i, i, i, dp, dp]
+        L.orc_sur_samples.argtypes = [p, C.c_long, ip, dp, dp, ip]
         _lib = L
     return _lib
 
@@ -270,6 +273,17 @@ class Oracle:
 
     def tir_count(self) -> int:
         return lib().orc_tir_count(self.h)
+
+    def sur_samples(self, idx):
+        """Learned-remap rows idx [n][3] = (zone, kind, source angle):
+        features [n][16], exact targets [n][27], validity [n] (see
+        orc_sur_sample)."""
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32).reshape(-1, 3))
+        n = len(idx)
+        X, Y = np.zeros((n, 16)), np.zeros((n, 27))
+        v = np.zeros(n, dtype=np.int32)
+        lib().orc_sur_samples(self.h, n, _ip(idx), _dp(X), _dp(Y), _ip(v))
+        return X, Y, v
 
 
 def run(prob, n_steps=None, dt=None, cfl=None):

@@ -355,6 +355,7 @@ typedef struct {
   double *v0, *al0, *ph0;      /* previous background (time remap) */
   double *ka, *ks, *fe;        /* [s][zone][e] */
   int has_bg, remap_pending;
+  int has_prev;                /* v0, al0, ph0 hold a previous background */
   double phase_norm;
   /* last-step outputs */
   double *dN, *dE, *dP;        /* [s][zone], [s][zone], [s][zone][3] */
@@ -444,6 +445,7 @@ void orc_set_background(orc_t *o, const double *v, const double *al, const doubl
     memcpy(o->al0, o->al, sizeof(double)*Z);
     memcpy(o->ph0, o->ph, sizeof(double)*Z);
     o->remap_pending = 1;
+    o->has_prev = 1;
   }
   memcpy(o->v, v, sizeof(double)*3*Z);
   memcpy(o->al, al, sizeof(double)*Z);
@@ -1058,3 +1060,109 @@ void orc_grid(const orc_t *o, double *eps_c, double *dgam, double *mu, double *d
   memcpy(vol, o->vol, sizeof(double) * nz(o));
 }
 int orc_tir_count(const orc_t *o) { return o->n_tir; }
+
+/* ------------------------------------------------------------------------- */
+/* Learned-remap rows (test reference of the library's sample generator).    */
+/* A row is (zone, kind, source angle).  kind 0: the zone's time remap,      */
+/* previous -> current background.  kind 1 + 6 f + r: remap r of the zone's  */
+/* face f (0 inner r, 1 outer r, 2 lower polar or the column's periodic      */
+/* polar face, 3 upper polar, 4 azimuthal); r = 0..3 stencil cell r -> face, */
+/* r = 4, 5 face -> cell 1 (P), 2 (Q).  Same faces and frames as the step    */
+/* above.  Outputs the 16 features and the exact trilinear weights of        */
+/* Sec. 3.2 on the offsets {-1,0,1}^3 (group, mu index, Phi index), index    */
+/* 9 (de+1) + 3 (dm+1) + (dp+1), Phi offsets taken to the nearest periodic   */
+/* image.  Returns 1 (usable), 2 (a nonzero weight outside the offsets;      */
+/* targ = 0) or 0 (no such remap; feat = targ = 0).                          */
+/* ------------------------------------------------------------------------- */
+static int sur_face(orc_t *o, int zone, int fidx, face_t *F) {
+  int a = zone % o->n_r, b = zone / o->n_r;
+  int sph = o->geom == ORC_SPHERICAL;
+  switch (fidx) {
+    case 0: return make_r_face(o, b, a, F);
+    case 1: return make_r_face(o, b, a + 1, F);
+    case 2:
+      if (!sph) return 0;
+      if (o->periodic_th) return make_periodic_face(o, zone, 1, F);
+      return b >= 1 ? make_th_face(o, a, b, F) : 0;
+    case 3:
+      if (!sph || o->periodic_th) return 0;
+      return b + 1 < o->n_th ? make_th_face(o, a, b + 1, F) : 0;
+    case 4:
+      return sph ? make_periodic_face(o, zone, 2, F) : 0;
+  }
+  return 0;
+}
+
+int orc_sur_sample(orc_t *o, int zone, int kind, int ang, double *feat, double *targ) {
+  for (int q = 0; q < 16; ++q) feat[q] = 0.0;
+  for (int q = 0; q < 27; ++q) targ[q] = 0.0;
+  if (zone < 0 || zone >= nz(o) || kind < 0 || kind > 30 || ang < 0 || ang >= o->n_ang) return 0;
+  loc_t X, Y;
+  int axis;
+  if (kind == 0) {
+    if (!o->has_prev) return 0;
+    X.th = Y.th = 0.0; X.ph = Y.ph = 0.0;
+    for (int m = 0; m < 3; ++m) { X.v[m] = o->v0[3*zone+m]; Y.v[m] = o->v[3*zone+m]; }
+    X.al = o->al0[zone]; X.cf = o->ph0[zone];
+    Y.al = o->al[zone]; Y.cf = o->ph[zone];
+    axis = KICK_TIME;
+  } else {
+    int fidx = (kind - 1) / 6, r = (kind - 1) % 6;
+    face_t F;
+    if (!sur_face(o, zone, fidx, &F)) return 0;
+    int slot = r < 4 ? r : r - 3;
+    if (F.z[slot] < 0) return 0;
+    if (r < 4) { X = F.L[slot]; Y = F.S; }
+    else { X = F.S; Y = F.L[slot]; }
+    axis = F.axis;
+  }
+  double G[9], n[3];
+  orc_rotation(X.th, X.ph, Y.th, Y.ph, G);
+  bin_dir(o, ang, n);
+  /* features (the network's inputs) */
+  for (int c = 0; c < 3; ++c) {
+    feat[c] = n[c];
+    feat[3+c] = X.v[c];
+    feat[6+c] = G[c]*Y.v[0] + G[3+c]*Y.v[1] + G[6+c]*Y.v[2];   /* G^T v_Y */
+  }
+  feat[9] = 0.5*(G[7] - G[5]);
+  feat[10] = 0.5*(G[2] - G[6]);
+  feat[11] = 0.5*(G[3] - G[1]);
+  if (axis >= 0 && axis < 3) feat[12+axis] = log(X.al / Y.al);
+  feat[15] = 2.0*log(X.cf / Y.cf);
+  /* exact weights */
+  double rho, mus, Phis;
+  orc_chain(X.v, X.al, X.cf, Y.v, Y.al, Y.cf, G, axis, n, &rho, &mus, &Phis);
+  int m, jL, kL;
+  double we, wm, wp;
+  orc_weights_eps(rho, o->R, &m, &we);
+  orc_weights_mu(mus, o->n_mu, o->mu, &jL, &wm);
+  orc_weights_phi(Phis, o->n_ph, &kL, &wp);
+  int j = ang / o->n_ph, k = ang % o->n_ph;
+  int jR = o->n_mu > 1 ? jL + 1 : jL;
+  int kR = (kL + 1) % o->n_ph;
+  int rep = 1;
+  for (int ie = 0; ie < 2; ++ie)
+    for (int ij = 0; ij < 2; ++ij)
+      for (int ik = 0; ik < 2; ++ik) {
+        double c = (ie ? we : 1.0 - we) * (ij ? wm : 1.0 - wm) * (ik ? wp : 1.0 - wp);
+        if (c == 0.0) continue;
+        int de = m + ie, dm = (ij ? jR : jL) - j, dp = (ik ? kR : kL) - k;
+        if (o->n_ph >= 3) {
+          if (2*dp >= o->n_ph) dp -= o->n_ph;
+          else if (2*dp < -o->n_ph) dp += o->n_ph;
+        }
+        if (de < -1 || de > 1 || dm < -1 || dm > 1 || dp < -1 || dp > 1) { rep = 0; continue; }
+        targ[9*(de+1) + 3*(dm+1) + (dp+1)] += c;
+      }
+  if (!rep) {
+    for (int q = 0; q < 27; ++q) targ[q] = 0.0;
+    return 2;
+  }
+  return 1;
+}
+
+void orc_sur_samples(orc_t *o, long n, const int *idx, double *feat, double *targ, int *valid) {
+  for (long i = 0; i < n; ++i)
+    valid[i] = orc_sur_sample(o, idx[3*i], idx[3*i+1], idx[3*i+2], feat + 16*i, targ + 27*i);
+}

@@ -86,6 +86,9 @@ def lib():
         L.bt_batch_destroy.argtypes = [vp]
         L.bt_profile.argtypes = [vp, i32]
         L.bt_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.bt_sur_samples.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+        L.bt_set_surrogate.argtypes = [vp, vp, C.c_double]
+        L.bt_sur_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.bt_sur_create.argtypes = [vp, C.POINTER(vp)]
         L.bt_sur_destroy.argtypes = [vp]
         L.bt_sur_set_params.argtypes = [vp, i32, vp]
@@ -265,6 +268,28 @@ class Transport:
     def set_launch_shape(self, nt: int):
         _check(lib().bt_set_launch_shape(self.h, int(nt)))
 
+    def sur_samples(self, idx):
+        """Learned-remap rows idx [n][3] (zone, kind, source angle) -> device
+        tensors X [n][16], Y [n][27], valid [n] (bt_sur_samples)."""
+        import torch
+        idx = torch.as_tensor(np.ascontiguousarray(np.asarray(idx, dtype=np.int32).reshape(-1, 3))).cuda()
+        n = idx.shape[0]
+        X = torch.empty((n, SUR_NIN), dtype=torch.float32, device="cuda")
+        Y = torch.empty((n, SUR_NOUT), dtype=torch.float32, device="cuda")
+        v = torch.empty(n, dtype=torch.int32, device="cuda")
+        _check(lib().bt_sur_samples(self.h, idx.data_ptr(), n, X.data_ptr(), Y.data_ptr(), v.data_ptr()))
+        return X, Y, v
+
+    def set_surrogate(self, sur, tol: float):
+        """Learned remap weights in every step (sur = None: exact weights)."""
+        self._sur = sur
+        _check(lib().bt_set_surrogate(self.h, sur.h if sur is not None else None, float(tol)))
+
+    def sur_stats(self):
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().bt_sur_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
     def profile(self, enable: bool):
         _check(lib().bt_profile(self.h, int(enable)))
 
@@ -274,7 +299,7 @@ class Transport:
         return ms.value, n.value
 
 
-K_TIME_REMAP, K_FLUX, K_OUTFLOW = 0, 1, 2
+K_TIME_REMAP, K_FLUX, K_OUTFLOW, K_SUR_TABLE = 0, 1, 2, 3
 
 
 class Batch:

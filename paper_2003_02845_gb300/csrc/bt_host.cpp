@@ -161,6 +161,25 @@ struct bt_handle {
   bool prof;
   std::vector<int> prof_id;
   std::vector<cudaEvent_t> prof_ev;
+  // learned remap (bt_set_surrogate)
+  bt_surrogate* sur = nullptr;
+  void* sur_tab = nullptr;                    // [zone][31][n_ang] weights
+  unsigned long long* sur_counts = nullptr;   // [2] rows evaluated, tripped
+  float sur_tol = 0.0f;
+};
+
+// The learned remap's network: parameters, normaliser, Adam state.
+struct bt_surrogate {
+  cudaStream_t stream = nullptr;
+  float* prm = nullptr;    // [kNParam] fp32 master parameters
+  float* grad = nullptr;   // [kNParam]
+  float* m = nullptr;      // Adam moments [kNTrain]
+  float* v = nullptr;
+  float* loss = nullptr;   // [1] loss of the last batch
+  int* flag = nullptr;     // [4] device-side error flags
+  double* stats = nullptr; // [32] feature sums for the normaliser
+  int n_sm = 0;
+  int64_t adam_t = 0;      // Adam step count
 };
 
 namespace {
@@ -508,6 +527,8 @@ struct ProfScope {
 int bt_destroy(bt_handle* h) {
   if (!h) return BT_OK;
   prof_clear(h);
+  if (h->sur_tab) cudaFree(h->sur_tab);
+  if (h->sur_counts) cudaFree(h->sur_counts);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;
   return BT_OK;
@@ -587,6 +608,7 @@ static void bind_state(bt_handle* h) {
   S.v_old = h->bg[old][0]; S.al_old = h->bg[old][1]; S.cf_old = h->bg[old][2];
   S.f = h->f[h->fcur];
   S.f_next = h->f[1 - h->fcur];
+  S.sur_tab = h->sur ? h->sur_tab : nullptr;
 }
 
 int bt_max_dt(bt_handle* h, double cfl, double* dt_out) {
@@ -609,6 +631,13 @@ int bt_max_dt(bt_handle* h, double cfl, double* dt_out) {
 static int step_enqueue(bt_handle* h, double dt) {
   bind_state(h);
   int e;
+  if (h->sur) {
+    ProfScope ps(h, BT_K_SUR_TABLE);
+    e = bt::launch_sur_table(h->tb, h->st, h->sur->prm, h->sur_tol, h->remap_pending ? 1 : 0, h->sur_tab,
+                             h->sur_counts, 4 * h->sur->n_sm, h->stream);
+    h->launches += 1;
+    if (e) return cuda_fail((cudaError_t)e, "learned remap table");
+  }
   if (h->remap_pending) {
     ProfScope ps(h, BT_K_TIME_REMAP);
     e = bt::launch_time_remap(h->tb, h->st, h->mixed, h->stream);
@@ -757,6 +786,41 @@ int bt_jhk(bt_handle* h, int mem, double* J, double* H, double* K) {
 
 int64_t bt_launch_count(const bt_handle* h) { return h ? h->launches : 0; }
 
+int bt_set_surrogate(bt_handle* h, bt_surrogate* s, double tol) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  if (s && !h->mixed) return fail(BT_ERR_ARG, "the learned remap runs in the mixed-precision path only");
+  if (s && !(tol >= 0.0) ) return fail(BT_ERR_ARG, "tol must be >= 0");
+  if (s && s->stream != h->stream) return fail(BT_ERR_ARG, "network and handle must share a stream");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_set_surrogate");
+  if (s && !h->sur_tab) {
+    e = cudaMalloc(&h->sur_tab, bt::sur_table_bytes(h->tb));
+    if (e == cudaSuccess) e = cudaMalloc(&h->sur_counts, 16);
+    if (e == cudaSuccess) e = cudaMemset(h->sur_counts, 0, 16);
+    if (e != cudaSuccess) {
+      if (h->sur_tab) cudaFree(h->sur_tab);
+      h->sur_tab = nullptr;
+      return cuda_fail(e, "learned remap table");
+    }
+  }
+  h->sur = s;
+  h->sur_tol = (float)tol;
+  return BT_OK;
+}
+
+int bt_sur_stats(bt_handle* h, int64_t* n_eval, int64_t* n_trip) {
+  if (!h || !n_eval || !n_trip) return fail(BT_ERR_ARG, "NULL");
+  unsigned long long c[2] = {0, 0};
+  if (h->sur_counts) {
+    cudaError_t e = cudaMemcpyAsync(c, h->sur_counts, 16, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bt_sur_stats");
+  }
+  *n_eval = (int64_t)c[0];
+  *n_trip = (int64_t)c[1];
+  return check_flag(h);
+}
+
 int bt_sur_samples(bt_handle* h, const int32_t* idx, int64_t n, float* X, float* Y, int32_t* valid) {
   if (!h || (n > 0 && (!idx || !X || !Y || !valid)) || n < 0) return fail(BT_ERR_ARG, "NULL or n < 0");
   if (h->n_bg < 2) return fail(BT_ERR_STATE, "bt_sur_samples needs a previous and a current background");
@@ -840,6 +904,8 @@ int bt_batch_step(bt_batch* b, const double* dt) {
     key.push_back(h->remap_pending ? 1 : 0);
     key.push_back(dt[i]);
     key.push_back(h->nt);
+    key.push_back(h->sur ? 1.0 : 0.0);
+    key.push_back(h->sur_tol);
   }
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
@@ -880,7 +946,7 @@ int bt_batch_step(bt_batch* b, const double* dt) {
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
   b->graph_launches += 1;
   for (bt_handle* h : b->m) {
-    h->launches += (h->remap_pending ? 1 : 0) + 3;
+    h->launches += (h->remap_pending ? 1 : 0) + (h->sur ? 1 : 0) + 3;
     h->remap_pending = false;
     h->fcur = 1 - h->fcur;
   }
@@ -929,18 +995,6 @@ int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launche
 // ---------------------------------------------------------------------------
 // The learned remap's network (bt_sur_*): parameters, normaliser, Adam state.
 // ---------------------------------------------------------------------------
-struct bt_surrogate {
-  cudaStream_t stream = nullptr;
-  float* prm = nullptr;    // [kNParam] fp32 master parameters
-  float* grad = nullptr;   // [kNParam]
-  float* m = nullptr;      // Adam moments [kNTrain]
-  float* v = nullptr;
-  float* loss = nullptr;   // [1] loss of the last batch
-  int* flag = nullptr;     // [4] device-side error flags
-  double* stats = nullptr; // [32] feature sums for the normaliser
-  int n_sm = 0;
-  int64_t adam_t = 0;      // Adam step count
-};
 
 namespace {
 

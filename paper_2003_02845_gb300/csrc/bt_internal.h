@@ -67,6 +67,9 @@ struct State {
   int* flag;            // [4] error flags (non-finite result, ...)
   double* qye;          // [zone] lepton-number source term of the last step
   double phase_norm;    // 1/h^3 factor of the hydro source terms
+  // learned remap: per (zone, remap kind, source angle) weights of the
+  // float32 path (nullptr: the exact weights are computed in the kernels)
+  const void* sur_tab;
 };
 
 struct LaunchCfg {
@@ -86,6 +89,12 @@ int launch_jhk(const Tables& T, const State& S, int mixed, double* J, double* H,
 int launch_check_finite(const Tables& T, const State& S, int mixed, void* stream);
 // learned remap: features X [n][16], exact targets Y [n][27] and validity of
 // the rows idx [n][3] = (zone, kind, source angle)
+// learned remap: fill st.sur_tab with the network's weights (judged against
+// the exact ones; tripped rows take the exact weights).  counts [2]: rows
+// evaluated, rows tripped (uint64, accumulated).
+int launch_sur_table(const Tables& T, const State& S, const float* prm, float tol, int with_time, void* tab,
+                     unsigned long long* counts, int grid, void* stream);
+size_t sur_table_bytes(const Tables& T);
 int launch_sur_samples(const Tables& T, const State& S, const int* idx, long long n, float* X, float* Y, int* valid,
                        void* stream);
 size_t flux_smem_bytes(const Tables& T, int mixed, int nt);

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "bt_internal.h"
+#include "bt_tc.cuh"
 
 namespace bt {
 
@@ -607,6 +608,7 @@ struct FaceT {
 };
 
 constexpr int kFaces = 5;
+constexpr int kSurKindsAll = 1 + 6 * kFaces;   // remap kinds of a zone (learned remap table)
 
 // dN accumulator type: float64 for the FP64 path; float for the mixed path,
 // whose per-zone content totals are tracked exactly (double-float) and
@@ -950,8 +952,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
         int slot = r < 4 ? r : r - 3;
         const T* G = F.G[slot] ? GF + 9 * slot : nullptr;
         Wt<T> w;
-        if (r < 4) chain_weights(tb, S.mu, S.n0, S.n1, S.n2, LF[slot], Ls, G, 0, F.axis, ang, Rg, w);
-        else chain_weights(tb, S.mu, S.n0, S.n1, S.n2, Ls, LF[slot], G, 1, F.axis, ang, Rg, w);
+        if (sizeof(T) == 4 && st.sur_tab) {
+          // learned remap: the table row of (zone, face fidx, remap r)
+          w = reinterpret_cast<const Wt<T>*>(st.sur_tab)[((size_t)zone * kSurKindsAll + 1 + 6 * fidx + r) * NA + ang];
+        } else if (r < 4) {
+          chain_weights(tb, S.mu, S.n0, S.n1, S.n2, LF[slot], Ls, G, 0, F.axis, ang, Rg, w);
+        } else {
+          chain_weights(tb, S.mu, S.n0, S.n1, S.n2, Ls, LF[slot], G, 1, F.axis, ang, Rg, w);
+        }
         S.W[r * NA + ang] = w;
       }
       // face bins: Eulerian energy factor and normal coordinate velocity
@@ -1435,8 +1443,12 @@ __global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
   make_loc(X, st.v_old + 3 * zone, st.al_old[zone], st.cf_old[zone]);
   make_loc(Y, st.v + 3 * zone, st.al[zone], st.cf[zone]);
   const T Rg = (T)tb.R;
-  for (int ang = tid; ang < NA; ang += kThreads)
-    chain_weights(tb, S.mu, S.n0, S.n1, S.n2, X, Y, (const T*)nullptr, 0, AX_TIME, ang, Rg, S.W[ang]);
+  for (int ang = tid; ang < NA; ang += kThreads) {
+    if (sizeof(T) == 4 && st.sur_tab)
+      S.W[ang] = reinterpret_cast<const Wt<T>*>(st.sur_tab)[(size_t)zone * kSurKindsAll * NA + ang];
+    else
+      chain_weights(tb, S.mu, S.n0, S.n1, S.n2, X, Y, (const T*)nullptr, 0, AX_TIME, ang, Rg, S.W[ang]);
+  }
   __syncthreads();
   const int em = gact ? S.W[gb].m : 0;
   const T ew = gact ? S.W[gb].we : T(0);
@@ -1642,7 +1654,6 @@ __global__ void k_jhk(Tables tb, State st, double* J, double* H, double* K) {
 // 1 + 6 fidx + r is remap r of the zone's face fidx (r < 4: stencil cell r ->
 // face, r = 4, 5: face -> cell 1, 2; Sec. 3.3).
 // ---------------------------------------------------------------------------
-constexpr int kSurKinds = 1 + 6 * kFaces;
 
 struct RemapRow {
   const double* vX;
@@ -1756,7 +1767,7 @@ __global__ void k_sur_samples(Tables tb, State st, const int* idx, long long n, 
     int v = 0;
     FaceDesc F;
     RemapRow R;
-    if (zone >= 0 && zone < tb.n_zone && kind >= 0 && kind < kSurKinds && ang >= 0 && ang < tb.n_ang &&
+    if (zone >= 0 && zone < tb.n_zone && kind >= 0 && kind < kSurKindsAll && ang >= 0 && ang < tb.n_ang &&
         sur_row(tb, st, zone, kind, F, R)) {
       sur_features(tb, R, ang, f);
       Loc<double> LX, LY;
@@ -1771,6 +1782,169 @@ __global__ void k_sur_samples(Tables tb, State st, const int* idx, long long n, 
     for (int q = 0; q < 27; ++q) Y[27 * i + q] = (float)y[q];
     valid[i] = v;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Learned remap in the step: one CTA (one warpgroup) per zone at a time
+// evaluates the network on the zone's 31 x n_ang remap rows (tensor cores,
+// 128-row tiles), projects each predicted distribution onto the trilinear
+// family by its mean offset per axis (exact when the prediction equals the
+// exact weights, which are trilinear), and judges it against the exact
+// float32 weights of the same row: a row whose mean offsets differ by tol or
+// more on any axis trips and takes the exact weights.  Both weight forms sum
+// to one per axis, so number is conserved either way.
+// ---------------------------------------------------------------------------
+struct SurXfer {
+  Loc<float> X, Y;
+  float G[9];
+  float feat[13];   // features 3..15 of every row of this remap
+  int hasG, gT, axis, ok;
+};
+
+constexpr int kSurT = 128;
+constexpr size_t kSurW = (tc::kMlpWBytes + 127) & ~size_t(127);
+constexpr size_t kSurX = kSurW;
+constexpr size_t kSurH = kSurX + 4096;
+constexpr size_t kSurXf = kSurH + 16384;
+constexpr size_t kSurDir = kSurXf + ((sizeof(SurXfer) * kSurKindsAll + 127) & ~size_t(127));
+constexpr size_t kSurBar = kSurDir + 4 * (3 * kMaxAng + kMaxMu);
+constexpr size_t kSurBytes = kSurBar + 64;
+
+__device__ __forceinline__ float mean_offset(const float* p, int axis) {
+  // sum over the 27 entries of offset * weight along one axis
+  float s = 0.0f;
+  for (int q = 0; q < 27; ++q) {
+    const int d = axis == 0 ? q / 9 : (axis == 1 ? (q / 3) % 3 : q % 3);
+    if (d == 0) s -= p[q];
+    else if (d == 2) s += p[q];
+  }
+  return s;
+}
+
+__global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const float* __restrict__ prm, float tol,
+                                                     int with_time, Wt<float>* __restrict__ tab,
+                                                     unsigned long long* counts) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const tc::MlpW w = tc::carve_w(smem);
+  unsigned char* Xs = smem + kSurX;
+  unsigned char* Hs = smem + kSurH;
+  SurXfer* xf = reinterpret_cast<SurXfer*>(smem + kSurXf);
+  float* n0 = reinterpret_cast<float*>(smem + kSurDir);
+  float* n1 = n0 + kMaxAng;
+  float* n2 = n1 + kMaxAng;
+  float* smu = n2 + kMaxAng;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kSurBar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kSurBar + 8);
+  const int t = threadIdx.x;
+  const int NA = tb.n_ang, NPH = tb.n_ph, NMU = tb.n_mu;
+  tc::stage_w(w, prm);
+  for (int q = t; q < NA; q += kSurT) {
+    const int j = q / NPH, k = q % NPH;
+    n0[q] = (float)tb.mu[j];
+    n1[q] = (float)(tb.smu[j] * tb.cph[k]);
+    n2[q] = (float)(tb.smu[j] * tb.sph[k]);
+  }
+  for (int q = t; q < NMU; q += kSurT) smu[q] = (float)tb.mu[q];
+  if (t == 0) tc::bar_init(bar);
+  if (t < 32) tc::tmem_alloc(slot, 64);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *slot;
+  unsigned phase = 0;
+  bool ok = true;
+  unsigned long long n_eval = 0, n_trip = 0;
+  const float Rf = (float)tb.R;
+  const int rows = kSurKindsAll * NA;
+  for (int zone = blockIdx.x; zone < tb.n_zone && ok; zone += gridDim.x) {
+    if (t < kSurKindsAll) {
+      SurXfer& x = xf[t];
+      FaceDesc F;
+      RemapRow R;
+      x.ok = (t > 0 || with_time) && sur_row(tb, st, zone, t, F, R);
+      if (x.ok) {
+        double f[16];
+        sur_features(tb, R, 0, f);
+        for (int q = 0; q < 13; ++q) x.feat[q] = (float)f[3 + q];
+        make_loc(x.X, R.vX, R.alX, R.cfX);
+        make_loc(x.Y, R.vY, R.alY, R.cfY);
+        x.hasG = R.G != nullptr;
+        for (int q = 0; q < 9; ++q) x.G[q] = R.G ? (float)R.G[q] : 0.0f;
+        x.gT = R.gT;
+        x.axis = R.axis;
+      }
+    }
+    __syncthreads();
+    for (int base = 0; base < rows && ok; base += kSurT) {
+      const int q = base + t;
+      const int kind = q / NA, ang = q % NA;
+      const bool valid = q < rows && xf[kind].ok;
+      float x[16], z[32], p[27];
+      if (valid) {
+        const SurXfer& X = xf[kind];
+        x[0] = n0[ang]; x[1] = n1[ang]; x[2] = n2[ang];
+#pragma unroll
+        for (int i = 0; i < 13; ++i) x[3 + i] = X.feat[i];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = (x[i] - w.mean[i]) * w.scale[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = 0.0f;
+      }
+      ok = tc::tile_forward(w, Xs, Hs, tmem, bar, phase, x, z, st.flag);
+      if (!ok || !valid) continue;
+      tc::softmax27(z, p);
+      const SurXfer& X = xf[kind];
+      // exact weights of the row (the judge and the fallback)
+      Wt<float> ex;
+      const float nd[3] = {n0[ang], n1[ang], n2[ang]};
+      chain_weights_dir<float>(tb, smu, nd, X.X, X.Y, X.hasG ? X.G : nullptr, X.gT, X.axis, Rf, ex);
+      const int j = ang / NPH, k = ang % NPH;
+      const float ee = (float)ex.m + ex.we;
+      const float em = (float)(ex.jL - j) + ex.wmu;
+      const float ep = (float)phi_offset(ex.kL - k, NPH) + ex.wph;
+      const float de = mean_offset(p, 0), dm = mean_offset(p, 1), dp = mean_offset(p, 2);
+      Wt<float> out = ex;
+      const bool trip = !(fabsf(de - ee) < tol && fabsf(dm - em) < tol && fabsf(dp - ep) < tol);
+      if (!trip) {
+        const float fe = floorf(de), fm = floorf(dm), fp = floorf(dp);
+        out.m = (short)fe;
+        out.we = de - fe;
+        int jl = j + (int)fm;
+        float wm = dm - fm;
+        if (NMU == 1) { jl = 0; wm = 0.0f; }
+        else if (jl < 0) { jl = 0; wm = 0.0f; }
+        else if (jl > NMU - 2) { jl = NMU - 2; wm = 1.0f; }
+        out.jL = (short)jl;
+        out.wmu = wm;
+        if (NPH == 1) { out.kL = 0; out.wph = 0.0f; }
+        else {
+          int kl = (k + (int)fp) % NPH;
+          if (kl < 0) kl += NPH;
+          out.kL = (short)kl;
+          out.wph = dp - fp;
+        }
+        out.pad = 0;
+      }
+      tab[((size_t)zone * kSurKindsAll + kind) * NA + ang] = out;
+      ++n_eval;
+      n_trip += trip ? 1 : 0;
+    }
+    __syncthreads();
+  }
+  if (!ok && t == 0) tc::bar_wait(bar, phase ^ 1u, nullptr);
+  for (int o = 16; o > 0; o >>= 1) {
+    n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
+    n_trip += __shfl_xor_sync(0xffffffffu, n_trip, o);
+  }
+  if ((t & 31) == 0) {
+    atomicAdd(counts, n_eval);
+    atomicAdd(counts + 1, n_trip);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (t < 32) tc::tmem_dealloc(tmem, 64);
 }
 
 template <typename T, int NT>
@@ -1821,6 +1995,7 @@ int prepare_kernels() {
   BT_SET((k_flux_collide<double, 512>));
   BT_SET((k_time_remap<float>));
   BT_SET((k_time_remap<double>));
+  BT_SET(k_sur_table);
 #undef BT_SET
   return (int)e;
 }
@@ -1887,6 +2062,16 @@ int launch_jhk(const Tables& tb, const State& st, int mixed, double* J, double* 
 }
 
 int launch_check_finite(const Tables&, const State&, int, void*) { return 0; }
+
+size_t sur_table_bytes(const Tables& tb) { return sizeof(Wt<float>) * (size_t)tb.n_zone * kSurKindsAll * tb.n_ang; }
+
+int launch_sur_table(const Tables& tb, const State& st, const float* prm, float tol, int with_time, void* tab,
+                     unsigned long long* counts, int grid, void* stream) {
+  const int g = grid < tb.n_zone ? grid : tb.n_zone;
+  k_sur_table<<<g, kSurT, kSurBytes, (cudaStream_t)stream>>>(tb, st, prm, tol, with_time,
+                                                             reinterpret_cast<Wt<float>*>(tab), counts);
+  return (int)cudaGetLastError();
+}
 
 int launch_sur_samples(const Tables& tb, const State& st, const int* idx, long long n, float* X, float* Y, int* valid,
                        void* stream) {

@@ -267,6 +267,28 @@ def config5_problems(seed=None) -> List[Problem]:
             cc2d(512, 128, 20, 16, 8, sc, base + 2, "config5_p2_512x128x20x128x6")]
 
 
+def config4_backgrounds(k: int, n_r=256, n_theta=64, n_e=12, scales=(1.0, 0.5, 0.2)):
+    """Background pair k of the learned remap's data: k = 0..15 make the
+    training set, k >= 16 are held out.  The config-3 recipe with its own
+    perturbation seed, shock radius uniform in [1e7, 3e7] cm and infall
+    amplitude uniform in [0.1, 0.3] (both drawn from the pair's seed)."""
+    rng = np.random.default_rng(BASE_SEED + 400 + k)
+    r_shock = rng.uniform(1e7, 3e7)
+    v_infall = rng.uniform(0.1, 0.3)
+    r_edges = np.geomspace(1e6, 1e8, n_r + 1)
+    eps_edges = np.geomspace(2.0, 200.0, n_e + 1)
+    return cc_background_pair(r_edges, n_theta, eps_edges, list(scales), BASE_SEED + 500 + k,
+                              r_shock=r_shock, v_infall=v_infall)
+
+
+def sur_rows(n_zone: int, n_ang: int, n: int, seed: int) -> np.ndarray:
+    """n remap rows (zone, kind, source angle), uniform over zones, the 31
+    remap kinds of a zone and the source angles: [n][3] int32."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.integers(0, n_zone, n), rng.integers(0, 31, n), rng.integers(0, n_ang, n)],
+                    axis=1).astype(np.int32)
+
+
 # ---------------------------------------------------------------------------
 # Small cases (oracle physics pins and GPU parity at oracle-friendly sizes)
 # ---------------------------------------------------------------------------

@@ -105,3 +105,106 @@ def test_training_reduces_loss(gpu):
     assert log[-1] < log[0]
     # the excess over the entropy floor shrinks at least tenfold
     assert L1 - ent < 0.1 * (L0 - ent), (L0, L1, ent)
+
+
+# ---------------------------------------------------------------------------
+# Rows of the exact remap: the library's generator against the oracle's
+# ---------------------------------------------------------------------------
+def _two_backgrounds(obj, p):
+    obj.set_background(p.backgrounds[0])
+    obj.set_background(p.backgrounds[1])
+
+
+def _probs_for_rows():
+    from paper_2003_02845_gb300 import workloads as W
+    return [W.random_2d(41, n_r=9, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=1),
+            W.random_2d(42, n_r=6, n_theta=4, n_e=3, n_mu=5, n_phi=7, n_s=1, r_min=0.0),
+            W.random_column(43, n_r=8, n_e=5, n_mu=6, n_phi=4, n_s=1),
+            W.slab_diffusion(kappa_s=30.0, dz=0.05, z_max=0.3, n_mu=6)]
+
+
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
+def test_rows_match_oracle(orc, gpu, case):
+    p = _probs_for_rows()[case]
+    if len(p.backgrounds) < 2:
+        p.backgrounds = [p.backgrounds[0], p.backgrounds[0]]
+    rng = np.random.default_rng(50 + case)
+    n = 6000
+    idx = np.stack([rng.integers(0, p.n_zone, n), rng.integers(0, 31, n), rng.integers(0, p.n_ang, n)], 1)
+    idx[:5] = [(-1, 0, 0), (0, 31, 0), (0, 0, p.n_ang), (p.n_zone, 1, 0), (0, -1, 0)]   # out of range
+    t = gpu.Transport(p, "mixed")
+    _two_backgrounds(t, p)
+    Xg, Yg, vg = [a.cpu().numpy() for a in t.sur_samples(idx)]
+    o = orc.Oracle(p)
+    _two_backgrounds(o, p)
+    Xo, Yo, vo = o.sur_samples(idx)
+    assert np.array_equal(vg, vo)
+    assert list(vg[:5]) == [0] * 5
+    assert (vg == 1).sum() > n // 4
+    # float64 on both sides, stored as float32 by the library
+    assert np.all(np.abs(Xg - Xo) <= 1e-6 * np.maximum(1.0, np.abs(Xo)))
+    assert np.abs(Yg - Yo).max() <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# The learned remap inside the step
+# ---------------------------------------------------------------------------
+def _trained_network(gpu, p, epochs=6, n=60000, seed=60):
+    """A network trained on rows of p's exact remap (both backgrounds)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    idx = np.stack([rng.integers(0, p.n_zone, n), rng.integers(0, 31, n), rng.integers(0, p.n_ang, n)], 1)
+    t = gpu.Transport(p, "mixed")
+    _two_backgrounds(t, p)
+    X, Y, v = t.sur_samples(idx)
+    keep = v == 1
+    X, Y = X[keep].contiguous(), Y[keep].contiguous()
+    s = gpu.Surrogate()
+    s.set_params(mlp.init_params(seed).astype(np.float32))
+    s.fit_normalizer(X)
+    s.train(X, Y, epochs=epochs, batch=1024, lr=3e-3, lr_final=1e-4)
+    return s
+
+
+def _run(gpu, p, steps, sur=None, tol=0.0, dt=0.01):
+    t = gpu.Transport(p, "mixed")
+    if sur is not None:
+        t.set_surrogate(sur, tol)
+    t.set_background(p.backgrounds[0])
+    t.set_f(p.f0)
+    for k in range(steps):
+        t.set_background(p.backgrounds[(k + 1) % 2])
+        t.step(dt)
+    return t
+
+
+def test_zero_tolerance_reproduces_the_exact_mixed_step(gpu):
+    from paper_2003_02845_gb300 import workloads as W
+    p = W.random_2d(44, n_r=8, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=2)
+    s = gpu.Surrogate()
+    s.set_params(_params(7))
+    a = _run(gpu, p, 5)
+    b = _run(gpu, p, 5, s, 0.0)
+    assert np.array_equal(a.get_f(), b.get_f())
+    n_eval, n_trip = b.sur_stats()
+    assert n_eval > 0 and n_trip == n_eval
+
+
+def test_learned_remap_step_conserves_and_counts(gpu):
+    from paper_2003_02845_gb300 import workloads as W
+    p = W.random_2d(45, n_r=8, n_theta=4, n_e=3, n_mu=4, n_phi=6, n_s=1)
+    for bg in p.backgrounds:
+        bg.kappa_a[:] = 0.0          # no emission or absorption: number is conserved
+    s = _trained_network(gpu, p, epochs=4, n=40000)
+    t = gpu.Transport(p, "mixed")
+    t.set_surrogate(s, 0.2)
+    t.set_background(p.backgrounds[0])
+    t.set_f(p.f0)
+    N0 = t.totals()[0]
+    for k in range(10):
+        t.set_background(p.backgrounds[(k + 1) % 2])
+        t.step(0.01)
+    N, _, No, _ = t.totals()
+    assert np.allclose(N + No, N0, rtol=1e-6, atol=0)
+    n_eval, n_trip = t.sur_stats()
+    assert n_eval > 0 and n_trip < n_eval      # the network is used on some rows
