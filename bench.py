@@ -134,9 +134,9 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 # workload, precision and launch shape, and valid only for the kernel source
 # it was taken on: a changed bt_kernels.cu reports null until re-captured.
 TRAFFIC = {
-    ("config3_cc2d_256x64x12x80x3", "mixed", 256):
+    ("config3_cc2d_256x64x12x80x3", "mixed", "fused/256"):
         (371.97e6, "85cb2f212c7785ccc48af3435cf2633ee70ea9baa0f04b0f2a4a6a882c4041d2"),
-    ("config3_cc2d_256x64x12x80x3", "fp64", 256):
+    ("config3_cc2d_256x64x12x80x3", "fp64", "fused/256"):
         (755.74e6, "85cb2f212c7785ccc48af3435cf2633ee70ea9baa0f04b0f2a4a6a882c4041d2"),
 }
 
@@ -235,8 +235,14 @@ def run_ours(args):
     for k in range(args.steps):
         one_step(args.warmup + args.steps + k)
     flux_ms, flux_n = t.profile_read(bt.K_FLUX)
+    zone_ms, zone_n = t.profile_read(bt.K_ZONE)
     remap_ms, remap_n = t.profile_read(bt.K_TIME_REMAP)
     t.profile(False)
+    split = bool(t.launch_shape & bt.SHAPE_SPLIT)
+    face_avg_ms = flux_ms / max(flux_n, 1)
+    if split:
+        # the split flux step: face pass + zone pass make one unit of work
+        flux_ms, flux_n = flux_ms + zone_ms, flux_n
 
     # end to end through the C ABI with host buffers: pinned host background in,
     # source terms out, every step
@@ -293,14 +299,14 @@ def run_ours(args):
             "l2": "inputs larger than L2 (f is %.0f MB per buffer)" % (bins * (4 if mixed else 8) / 1e6),
             "parallelism": "replicas" if world > 1 else "single GPU",
             "backgrounds": "B0/B1 alternate every step (time remap active)",
-            "launch_shape": t.launch_shape,
+            "launch_shape": bt.shape_name(t.launch_shape),
         },
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "e2e": {"value": world * units_per_step / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {
-            "kernel": "k_flux_collide<%s>" % ("float" if mixed else "double"),
+            "kernel": kernel_name(mixed, split),
             "bound": "alu",
             "achieved": achieved_tf,
             "peak": peak_tf,
@@ -308,10 +314,12 @@ def run_ours(args):
                 GB300_SMS, GB300_FP32_LANES, GB300_SM_GHZ, "" if mixed else " / 64 (float64)"),
             "unit": "TFLOP/s",
             "frac": achieved_tf / peak_tf,
-            "traffic": measured_traffic(prob.name, args.precision, t.launch_shape),
+            "traffic": measured_traffic(prob.name, args.precision, bt.shape_name(t.launch_shape)),
             "traffic_unit": "bytes per launch (ncu dram read + write)",
             "algorithmic_flops_per_bin": fpb,
             "avg_launch_ms": flux_avg_ms,
+            "face_pass_avg_ms": face_avg_ms if split else None,
+            "zone_pass_avg_ms": zone_ms / max(zone_n, 1) if split else None,
             "time_remap_avg_ms": remap_ms / max(remap_n, 1),
             "hbm": {"achieved": achieved_gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                     "frac": achieved_gbs / peak, "algorithmic_bytes_per_bin": bpb},
@@ -344,16 +352,23 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def kernel_name(mixed, split):
+    tn = "float" if mixed else "double"
+    if split:
+        return "k_flux_faces<%s> + k_zone_collide<%s> (split flux step)" % (tn, tn)
+    return "k_flux_collide<%s>" % tn
+
+
 def rel_l1(a, b):
     return float((a.double() - b.double()).abs().sum() / b.double().abs().sum())
 
 
-def run_steps(prob, dev, precision, steps, sur=None, tol=0.0):
+def run_steps(prob, dev, precision, steps, sur=None, tol=0.0, stream=None):
     """f (device tensor) after `steps` steps from f0 with the backgrounds
     alternating as in the timed run, dt from the Courant limit of B0."""
     import torch
     from paper_2003_02845_gb300 import bt
-    stream = torch.cuda.Stream()
+    stream = stream if stream is not None else torch.cuda.Stream()
     t = bt.Transport(prob, precision, stream=stream)
     if sur is not None:
         t.set_surrogate(sur, tol)
@@ -376,12 +391,14 @@ def learned_remap_block(prob, dev, args, ms_exact, f64):
     with it and measure its error at a few trip tolerances."""
     import torch
     from paper_2003_02845_gb300 import bt, learned_remap as LR, workloads as W
+    stream = torch.cuda.Stream()      # network, data and steps share it
     t0 = time.perf_counter()
     pairs = [W.config4_backgrounds(k) for k in range(16)]
-    X, Y = LR.training_set(prob, pairs, args.sur_samples, seed=777)
+    with torch.cuda.stream(stream):
+        X, Y = LR.training_set(prob, pairs, args.sur_samples, seed=777, stream=stream)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    net, log = LR.train(X, Y, epochs=args.sur_epochs, batch=4096)
+    net, log = LR.train(X, Y, epochs=args.sur_epochs, batch=4096, stream=stream)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     n_rows = int(X.shape[0])
@@ -390,7 +407,6 @@ def learned_remap_block(prob, dev, args, ms_exact, f64):
            "loss_per_epoch": [float(x) for x in log],
            "data_seconds": t1 - t0, "train_seconds": t2 - t1, "runs": []}
     for tol in args.sur_tols:
-        stream = torch.cuda.Stream()
         t = bt.Transport(prob, "mixed", stream=stream)
         net_s = net
         t.set_surrogate(net_s, tol)
@@ -416,7 +432,7 @@ def learned_remap_block(prob, dev, args, ms_exact, f64):
         tab_ms, tab_n = t.profile_read(bt.K_SUR_TABLE)
         t.profile(False)
         t.close()
-        fs, (n_eval, n_trip) = run_steps(prob, dev, "mixed", args.accuracy_steps, sur=net_s, tol=tol)
+        fs, (n_eval, n_trip) = run_steps(prob, dev, "mixed", args.accuracy_steps, sur=net_s, tol=tol, stream=stream)
         out["runs"].append({"tol_bins": tol, "ms_per_step": ms_sur, "value": prob.n_bins / (ms_sur * 1e-3),
                             "speed_vs_exact_mixed": ms_exact / ms_sur,
                             "table_kernel_ms": tab_ms / max(tab_n, 1),
@@ -470,7 +486,7 @@ def run_batch(args, rank, world):
         dts.append(m.max_dt(p.cfl))
     shapes = []
     for m, d, dt in zip(b.members, dev, dts):
-        shapes.append(m.autotune(dt) if args.autotune else m.launch_shape)
+        shapes.append(bt.shape_name(m.autotune(dt) if args.autotune else m.launch_shape))
     torch.cuda.synchronize()
     bins = sum(p.n_bins for p in probs)
 
@@ -534,8 +550,11 @@ def run_batch(args, rank, world):
         m.set_background_device(*dev[big][(k + 1) % 2])
         m.step(dts[big])
     flux_ms, flux_n = m.profile_read(bt.K_FLUX)
+    zone_ms, zone_n = m.profile_read(bt.K_ZONE)
     m.profile(False)
-    flux_avg_ms = flux_ms / max(flux_n, 1)
+    split = bool(m.launch_shape & bt.SHAPE_SPLIT)
+    face_avg_ms = flux_ms / max(flux_n, 1)
+    flux_avg_ms = (flux_ms + (zone_ms if split else 0.0)) / max(flux_n, 1)
     fpb = algorithmic_flops_per_bin(p)
     bpb = algorithmic_bytes_per_bin(p, mixed)
     achieved_tf = p.n_bins * fpb / (flux_avg_ms * 1e-3) / 1e12
@@ -571,7 +590,7 @@ def run_batch(args, rank, world):
         "clocks": clk.summary(),
         "e2e": {"value": world * bins / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {
-            "kernel": "k_flux_collide<%s> of %s" % ("float" if mixed else "double", p.name),
+            "kernel": "%s of %s" % (kernel_name(mixed, split), p.name),
             "bound": "alu",
             "achieved": achieved_tf,
             "peak": peak_tf,
@@ -582,6 +601,8 @@ def run_batch(args, rank, world):
             "traffic": None,
             "algorithmic_flops_per_bin": fpb,
             "avg_launch_ms": flux_avg_ms,
+            "face_pass_avg_ms": face_avg_ms if split else None,
+            "zone_pass_avg_ms": zone_ms / max(zone_n, 1) if split else None,
             "hbm": {"achieved": achieved_gbs, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
                     "frac": achieved_gbs / peak, "algorithmic_bytes_per_bin": bpb},
         },
@@ -620,16 +641,20 @@ def cpu_baseline(prob, budget_s=15.0, steps=1):
     rng = np.random.default_rng(0)
     n = 4
     spent, done_bins = 0.0, 0
+    per_zone = None
     while spent < budget_s:
+        if per_zone is not None:
+            # size the next chunk to the time left
+            n = int(min(2 * n, prob.n_zone, max(1, (budget_s - spent) / per_zone)))
         zones = rng.choice(prob.n_zone, min(n, prob.n_zone), replace=False)
         t0 = time.perf_counter()
         o.step_zones(dt, zones)
         el = time.perf_counter() - t0
         spent += el
         done_bins += len(zones) * prob.n_species * prob.n_eps * prob.n_ang
-        n = min(n * 2, prob.n_zone)
-        if n >= prob.n_zone and spent > 0.2 * budget_s:
-            break
+        per_zone = el / len(zones) if el > 0.05 else None
+        if per_zone is None:
+            n = min(n * 2, prob.n_zone)
     return {"value": done_bins / spent, "unit": UNIT, "cores": 1, "kind": "oracle",
             "seconds": spent, "bins": done_bins,
             "sample": "%d zone updates (all species, groups, angles) of %s by the single-threaded FP64 "

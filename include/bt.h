@@ -166,15 +166,24 @@ int64_t bt_launch_count(const bt_handle* h);
  * every launch of bt_step while enabled (enable = 1), for measurement.
  * bt_profile(h, 1) also clears the records.  bt_profile_read synchronises
  * the stream and returns, for kernel id BT_K_TIME_REMAP / BT_K_FLUX /
- * BT_K_OUTFLOW / BT_K_SUR_TABLE (the learned remap's table), the summed
+ * BT_K_OUTFLOW / BT_K_SUR_TABLE (the learned remap's table) / BT_K_ZONE (the
+ * split form's zone pass; BT_K_FLUX is then its face pass), the summed
  * duration in ms and the number of launches. */
-enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2, BT_K_SUR_TABLE = 3 };
+enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2, BT_K_SUR_TABLE = 3, BT_K_ZONE = 4 };
 int bt_profile(bt_handle* h, int enable);
 int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launches);
 
-/* Launch shape of the fused flux kernel: threads per CTA (128, 256 or 512;
- * default 256, or the choice cached by the autotuner).  The arithmetic of a
- * step does not depend on it. */
+/* Launch shape of the flux step.  128, 256 or 512: the fused form, one
+ * kernel in which each zone's CTA computes all of its faces (every interior
+ * face is computed by both neighbours) and then its collision solve, with
+ * that many threads per CTA (default 256, or the choice cached by the
+ * autotuner).  BT_SHAPE_SPLIT | 256 or | 512: the split form, a face pass in
+ * which every face is computed once (by the zone that owns it) and writes both
+ * neighbours' deposits, then a zone pass that gathers a zone's deposits in
+ * the fused order and solves its collision; it needs 6 x the f array in
+ * deposit rows, allocated when the shape is set.  Results are bitwise the same
+ * for every shape. */
+#define BT_SHAPE_SPLIT 0x10000
 int bt_launch_shape(const bt_handle* h, int* threads_per_cta);
 int bt_set_launch_shape(bt_handle* h, int threads_per_cta);
 
@@ -182,7 +191,8 @@ int bt_set_launch_shape(bt_handle* h, int threads_per_cta);
  * set) for every launch shape that fits, keeps the fastest, and -- if the
  * environment variable BT_TUNE_CACHE names a file -- records it there under a
  * key of the problem shape; bt_create reads that file.  The timing launches
- * overwrite the last-step moments but not f.  *chosen_nt may be NULL. */
+ * overwrite the last-step moments but not f.  The split shapes are tried
+ * only if their deposit rows can be allocated.  *chosen_nt may be NULL. */
 int bt_autotune(bt_handle* h, double dt, int* chosen_nt);
 
 /* Batched step: n independent problems (each its own configuration, e.g. of

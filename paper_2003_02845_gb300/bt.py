@@ -18,6 +18,7 @@ BT_OK = 0
 BT_GEOM_SPHERICAL, BT_GEOM_SLAB = 0, 1
 BT_FP64, BT_MIXED = 0, 1
 BT_MEM_HOST, BT_MEM_DEVICE = 0, 1
+SHAPE_SPLIT = 0x10000   # launch-shape flag of the split flux step
 
 _lib = None
 
@@ -299,7 +300,7 @@ class Transport:
         return ms.value, n.value
 
 
-K_TIME_REMAP, K_FLUX, K_OUTFLOW, K_SUR_TABLE = 0, 1, 2, 3
+K_TIME_REMAP, K_FLUX, K_OUTFLOW, K_SUR_TABLE, K_ZONE = 0, 1, 2, 3, 4
 
 
 class Batch:
@@ -441,3 +442,8 @@ class Surrogate:
         log = np.zeros(int(epochs), dtype=np.float32)
         _check(lib().bt_sur_train(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], C.byref(cfg), log.ctypes.data))
         return log
+
+
+def shape_name(nt: int) -> str:
+    """Readable launch shape: 'fused/256' or 'split/512'."""
+    return ("split/%d" if nt & SHAPE_SPLIT else "fused/%d") % (nt & 0xFFFF)

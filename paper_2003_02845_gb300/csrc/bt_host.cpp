@@ -161,6 +161,9 @@ struct bt_handle {
   bool prof;
   std::vector<int> prof_id;
   std::vector<cudaEvent_t> prof_ev;
+  // split form of the flux step: deposit rows and records (lazily allocated)
+  void* dep = nullptr;
+  void* rec = nullptr;
   // learned remap (bt_set_surrogate)
   bt_surrogate* sur = nullptr;
   void* sur_tab = nullptr;                    // [zone][31][n_ang] weights
@@ -319,6 +322,36 @@ size_t bt_workspace_bytes(const bt_config* cfg) {
   size_t ts[32];
   plan(cfg, P, ts);
   return P.total;
+}
+
+// deposit buffers of the split flux step (allocated on first use)
+static int ensure_split(bt_handle* h) {
+  if (h->dep && h->rec) return BT_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && !h->dep) e = cudaMalloc(&h->dep, bt::split_dep_bytes(h->tb, h->mixed));
+  if (e == cudaSuccess && !h->rec) e = cudaMalloc(&h->rec, bt::split_rec_bytes(h->tb));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (h->dep) cudaFree(h->dep);
+    if (h->rec) cudaFree(h->rec);
+    h->dep = h->rec = nullptr;
+    return cuda_fail(e, "split-step deposit buffers");
+  }
+  return BT_OK;
+}
+static void release_split(bt_handle* h) {
+  if (!h->dep && !h->rec) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->dep) cudaFree(h->dep);
+  if (h->rec) cudaFree(h->rec);
+  h->dep = h->rec = nullptr;
+}
+static bool valid_shape(int nt) {
+  return nt == 128 || nt == 256 || nt == 512 || nt == (bt::kShapeSplit | 256) || nt == (bt::kShapeSplit | 512);
+}
+static bool shape_fits(const bt_handle* h, int nt) {
+  return (long)bt::flux_smem_bytes(h->tb, h->mixed, nt) <= (long)bt::max_optin_smem() &&
+         bt::flux_occupancy(h->tb, h->mixed, nt) > 0;
 }
 
 int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
@@ -480,7 +513,8 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   h->nt = 256;
   {
     int cached = tune_lookup(h->tune_key);
-    if ((cached == 128 || cached == 256 || cached == 512) && bt::flux_occupancy(T, h->mixed, cached) > 0)
+    if (valid_shape(cached) && shape_fits(h, cached) &&
+        (!(cached & bt::kShapeSplit) || ensure_split(h) == BT_OK))
       h->nt = cached;
   }
   // shared memory per CTA must fit the opt-in limit
@@ -529,6 +563,8 @@ int bt_destroy(bt_handle* h) {
   prof_clear(h);
   if (h->sur_tab) cudaFree(h->sur_tab);
   if (h->sur_counts) cudaFree(h->sur_counts);
+  if (h->dep) cudaFree(h->dep);
+  if (h->rec) cudaFree(h->rec);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;
   return BT_OK;
@@ -647,9 +683,15 @@ static int step_enqueue(bt_handle* h, double dt) {
   }
   {
     ProfScope ps(h, BT_K_FLUX);
-    e = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, h->nt, h->stream);
+    e = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, h->nt, h->dep, h->rec, h->stream);
     h->launches += 1;
     if (e) return cuda_fail((cudaError_t)e, "flux/collide");
+  }
+  if (h->nt & bt::kShapeSplit) {
+    ProfScope ps(h, BT_K_ZONE);
+    e = bt::launch_zone_collide(h->tb, h->st, dt, h->mixed, h->dep, h->rec, h->stream);
+    h->launches += 1;
+    if (e) return cuda_fail((cudaError_t)e, "zone collide");
   }
   {
     ProfScope ps(h, BT_K_OUTFLOW);
@@ -673,22 +715,28 @@ int bt_autotune(bt_handle* h, double dt, int* chosen_nt) {
   if (!h->has_bg) return fail(BT_ERR_STATE, "bt_autotune before bt_set_background");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BT_ERR_DT, "dt must be positive and finite");
   bind_state(h);
-  const int cand[3] = {128, 256, 512};
-  const int lim = bt::max_optin_smem();
+  const int S = bt::kShapeSplit;
+  const int cand[5] = {128, 256, 512, S | 256, S | 512};
   float best = 0.f;
   int best_nt = h->nt;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   for (int nt : cand) {
-    if ((long)bt::flux_smem_bytes(h->tb, h->mixed, nt) > (long)lim) continue;
-    if (bt::flux_occupancy(h->tb, h->mixed, nt) <= 0) continue;
-    // the flux kernel reads f and writes the other buffer (and the moments),
-    // so repeated launches leave the state unchanged
-    int e = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, nt, h->stream);
+    if (!shape_fits(h, nt)) continue;
+    if ((nt & S) && ensure_split(h) != BT_OK) continue;   // no room for the deposit rows
+    // the flux step reads f and writes the other buffer (and the moments,
+    // and the split form's deposit rows), so repeated launches leave the
+    // state unchanged
+    auto run = [&]() {
+      int r = bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, nt, h->dep, h->rec, h->stream);
+      if (!r && (nt & S)) r = bt::launch_zone_collide(h->tb, h->st, dt, h->mixed, h->dep, h->rec, h->stream);
+      return r;
+    };
+    int e = run();
     if (e) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail((cudaError_t)e, "autotune"); }
     cudaEventRecord(a, h->stream);
-    for (int k = 0; k < 3; ++k) bt::launch_flux_collide(h->tb, h->st, dt, h->mixed, nt, h->stream);
+    for (int k = 0; k < 3; ++k) run();
     cudaEventRecord(b, h->stream);
     cudaError_t ce = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -700,6 +748,7 @@ int bt_autotune(bt_handle* h, double dt, int* chosen_nt) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->nt = best_nt;
+  if (!(best_nt & S)) release_split(h);
   tune_store(h->tune_key, best_nt);
   if (chosen_nt) *chosen_nt = best_nt;
   return check_flag(h);
@@ -713,11 +762,15 @@ int bt_launch_shape(const bt_handle* h, int* threads_per_cta) {
 
 int bt_set_launch_shape(bt_handle* h, int threads_per_cta) {
   if (!h) return fail(BT_ERR_ARG, "NULL");
-  if (threads_per_cta != 128 && threads_per_cta != 256 && threads_per_cta != 512)
-    return fail(BT_ERR_ARG, "threads_per_cta must be 128, 256 or 512");
-  if ((long)bt::flux_smem_bytes(h->tb, h->mixed, threads_per_cta) > (long)bt::max_optin_smem() ||
-      bt::flux_occupancy(h->tb, h->mixed, threads_per_cta) <= 0)
-    return fail(BT_ERR_ARG, "launch shape does not fit this problem");
+  if (!valid_shape(threads_per_cta))
+    return fail(BT_ERR_ARG, "launch shape must be 128, 256, 512, BT_SHAPE_SPLIT | 256 or BT_SHAPE_SPLIT | 512");
+  if (!shape_fits(h, threads_per_cta)) return fail(BT_ERR_ARG, "launch shape does not fit this problem");
+  if (threads_per_cta & bt::kShapeSplit) {
+    int rc = ensure_split(h);
+    if (rc != BT_OK) return rc;
+  } else {
+    release_split(h);
+  }
   h->nt = threads_per_cta;
   return BT_OK;
 }
@@ -946,7 +999,7 @@ int bt_batch_step(bt_batch* b, const double* dt) {
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
   b->graph_launches += 1;
   for (bt_handle* h : b->m) {
-    h->launches += (h->remap_pending ? 1 : 0) + (h->sur ? 1 : 0) + 3;
+    h->launches += (h->remap_pending ? 1 : 0) + (h->sur ? 1 : 0) + ((h->nt & bt::kShapeSplit) ? 1 : 0) + 3;
     h->remap_pending = false;
     h->fcur = 1 - h->fcur;
   }

@@ -81,7 +81,17 @@ struct LaunchCfg {
 // Kernel entry points (bt_kernels.cu).  All enqueue on `stream`; return a
 // cudaError_t as int.
 int launch_time_remap(const Tables& T, const State& S, int mixed, void* stream);
-int launch_flux_collide(const Tables& T, const State& S, double dt, int mixed, int nt, void* stream);
+// launch shape nt: threads per CTA (128, 256, 512), or kShapeSplit | threads
+// (256, 512) for the split form, whose face pass launch_flux_collide then
+// launches (the zone pass is launch_zone_collide); it needs the deposit
+// buffers dep (split_dep_bytes) and rec (split_rec_bytes)
+constexpr int kShapeSplit = 0x10000;
+int launch_flux_collide(const Tables& T, const State& S, double dt, int mixed, int nt, void* dep, void* rec,
+                        void* stream);
+// the zone pass of the split form (after launch_flux_collide's face pass)
+int launch_zone_collide(const Tables& T, const State& S, double dt, int mixed, void* dep, void* rec, void* stream);
+size_t split_dep_bytes(const Tables& T, int mixed);
+size_t split_rec_bytes(const Tables& T);
 int launch_totals(const Tables& T, const State& S, int mixed, double* d_out /*[2*n_s]*/, void* stream);
 int launch_accumulate_outflow(const Tables& T, const State& S, void* stream);
 int launch_max_rate(const Tables& T, const State& S, double* d_rate /*[1]*/, void* stream);

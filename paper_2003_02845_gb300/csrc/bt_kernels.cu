@@ -620,7 +620,9 @@ struct DNT<double> { using type = double; };
 template <>
 struct DNT<float> { using type = float; };
 
-// Shared-memory carve-up of the flux kernel.
+// Shared-memory carve-up of the flux kernel.  mode 0: fused faces +
+// collision of one zone; mode 1: the face pass (no dN); mode 2: the zone
+// pass (no stencil buffers or lists).
 template <typename T>
 struct FluxSmem {
   typename DNT<T>::type* dN;  // [ns][ne][nang]
@@ -668,7 +670,8 @@ struct FluxSmem {
 };
 
 template <typename T>
-__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, int nw, FluxSmem<T>* s, unsigned char* base) {
+__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, int nw, int mode, FluxSmem<T>* s,
+                                           unsigned char* base) {
   size_t o = 0;
   const int nbin = ne * nang;
 #define BT_TAKE(ptr, type, count)                              \
@@ -678,7 +681,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     o += sizeof(type) * (size_t)(count);                       \
   } while (0)
   BT_TAKE(bar, unsigned long long, 2);
-  BT_TAKE(dN, typename DNT<T>::type, (size_t)ns * nbin);
+  BT_TAKE(dN, typename DNT<T>::type, mode == 1 ? 0 : (size_t)ns * nbin);   // the face pass keeps no dN
   BT_TAKE(zu0, double, nang);
   BT_TAKE(ztau, double, nang);
   BT_TAKE(zcn, double, nang);
@@ -707,6 +710,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     size_t need_wc = o_c + sizeof(int) * (size_t)6 * nang - o_work;
     size_t need_col = sizeof(double) * (size_t)2 * nw * nang;
     size_t tot = stencil + (need_work > need_wc ? need_work : need_wc);
+    if (mode == 2) tot = 0;   // the zone pass stages no stencils
     if (need_col > tot) tot = need_col;
     if (s) {
       s->buf = reinterpret_cast<T*>(base + o_b);
@@ -717,8 +721,8 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     }
     o = o_b + tot;
   }
-  BT_TAKE(ent, AEnt<T>, 6 * 4 * nang);
-  BT_TAKE(off, short, 6 * (nang + 1));
+  BT_TAKE(ent, AEnt<T>, mode == 2 ? 0 : 6 * 4 * nang);
+  BT_TAKE(off, short, mode == 2 ? 0 : 6 * (nang + 1));
   BT_TAKE(n0, T, nang);
   BT_TAKE(n1, T, nang);
   BT_TAKE(n2, T, nang);
@@ -804,29 +808,6 @@ __device__ __forceinline__ int block_argmax(float key, int idx, float* rk, int* 
   __syncthreads();
   return bi;
 }
-
-// Conservation correction of a float gather: the values dep[0..n) must sum
-// to `target`; returns the residual of their float rounding (as a
-// double-float) and in *at the index of the largest |dep| that takes it.
-__device__ __forceinline__ ff conservation_residual(const float* dep, int n, ff target, ff* redf, float* rk, int* ri,
-                                                    int* at) {
-  ff part = ff{0.0f, 0.0f};
-  float bk = -1.0f;
-  int bi = 0x7fffffff;
-  for (int q = threadIdx.x; q < n; q += (int)blockDim.x) {
-    part = ff_add(part, dep[q]);
-    float k = fabsf(dep[q]);
-    if (k > bk) { bk = k; bi = q; }
-  }
-  ff tot = block_sum_ff(part, redf);
-  *at = block_argmax(bk, bi, rk, ri);
-  return ff_add(target, ff_neg(tot));
-}
-__device__ __forceinline__ ff conservation_residual(const double*, int, ff, ff*, float*, int*, int* at) {
-  *at = -1;
-  return ff{0.0f, 0.0f};
-}
-
 template <typename T>
 struct StoreG {   // g = D / (phi_s^6 u0_s dOmega) in the face frame (D per unit dGamma)
   T* dst; T cs; int na, b;
@@ -841,18 +822,55 @@ struct StoreT {
 // ---------------------------------------------------------------------------
 // Fused face fluxes + collision of one zone (Sec. 3.3, 3.5, 3.4)
 // ---------------------------------------------------------------------------
+// Split form: a face pass computes every face once (CTA per zone over the
+// faces it owns) and writes both neighbours' deposits; a zone pass gathers a
+// zone's deposits in the fused kernel's order and solves the collision.
+// Deposit rows live at slot 2 axis + (zone is the face's P side) of the
+// receiving zone: dep[(zone * 6 + slot) * n_s + s][group][angle].
+struct DepRec {
+  ff sum;           // exact total of the deposit row (mixed path)
+  double tn, te;    // outflow number and energy at infinity through the face
+};
+
+template <typename T>
+struct StoreDep {   // dep = sign * T[F]
+  T* dst; int na, b; T sign;
+  __device__ void operator()(int t, T acc) const { dst[t * na + b] = sign * acc; }
+};
+
+// a zone's faces owned by it in the face pass (each face has one owner)
+__device__ __forceinline__ bool face_owned(const Tables& tb, int a, int fidx) {
+  if (fidx == 0) return a == 0;
+  if (fidx == 2) return tb.periodic_th != 0;
+  return true;
+}
+
+// existence of a zone's face fidx, as make_face decides it
+__device__ __forceinline__ bool face_exists(const Tables& tb, int a, int b, int fidx) {
+  const int nr = tb.n_r;
+  if (fidx == 0 || fidx == 1) return tb.area_r[b * (nr + 1) + (fidx == 0 ? a : a + 1)] != 0.0;
+  if (tb.slab) return false;
+  if (fidx == 2 || fidx == 3) {
+    if (tb.periodic_th) return fidx == 2 && tb.area_t[a] != 0.0;
+    const int edge = fidx == 2 ? b : b + 1;
+    if (edge == 0 || edge == tb.n_th) return false;
+    return tb.area_t[edge * nr + a] != 0.0;
+  }
+  return tb.area_p[b * nr + a] != 0.0;
+}
+
 template <typename T>
 struct AddDN {   // dN += sign * T[F]
   typename DNT<T>::type* dn; int na, b; T sign;
   __device__ void operator()(int t, T acc) const { dn[t * na + b] += (typename DNT<T>::type)(sign * acc); }
 };
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT) : 1) k_flux_collide(Tables tb, State st, double dt) {
+template <typename T, int NT, int MODE>
+__device__ __forceinline__ void flux_body(const Tables& tb, const State& st, double dt, T* dep, DepRec* rec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using DN = typename DNT<T>::type;
   FluxSmem<T> S;
-  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, &S, smem_raw);
+  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, MODE, &S, smem_raw);
   const int zone = blockIdx.x;
   const int a = zone % tb.n_r, b = zone / tb.n_r;
   const int NE = tb.n_e, NA = tb.n_ang, NS = tb.n_s, NPH = tb.n_ph, NMU = tb.n_mu;
@@ -870,7 +888,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
   const bool use_tma = (rowbytes % 16u) == 0u;
   unsigned tphase = 0;               // parity of the next mbarrier phase to wait for
 
-  for (int q = tid; q < NS * nbin; q += NT) S.dN[q] = DN(0);
+  if (MODE != 1)
+    for (int q = tid; q < NS * nbin; q += NT) S.dN[q] = DN(0);
   for (int q = tid; q < NMU; q += NT) S.mu[q] = (T)tb.mu[q];
   for (int q = tid; q < NA; q += NT) {
     int j = q / NPH, k = q % NPH;
@@ -885,9 +904,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
   for (int q = tid; q < NS; q += NT) S.dtot[q] = ff{0.0f, 0.0f};
   if (tid == 0) mbar_init(S.bar, 1);
   const int nface = tb.slab ? 2 : kFaces;
-  if (tid < nface) {
+  if (MODE != 2 && tid < nface) {
     FaceDesc& Fd = S.F[tid];
-    if (!make_face(tb, st, a, b, tid, Fd)) {
+    if ((MODE == 1 && !face_owned(tb, a, tid)) || !make_face(tb, st, a, b, tid, Fd)) {
       Fd.type = -1;
     } else {
       FaceT<T>& ft = S.FT[tid];
@@ -929,16 +948,19 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
     while (f < nface && S.F[f].type < 0) ++f;
     return f;
   };
-  int first = next_face(-1);
+  int first = MODE == 2 ? nface : next_face(-1);
   if (first < nface) issue(first, 0);
 
-  for (int fidx = first; fidx < nface; fidx = next_face(fidx)) {
+  for (int fidx = first; MODE != 2 && fidx < nface; fidx = next_face(fidx)) {
     const FaceDesc& F = S.F[fidx];
     const FaceT<T>& ft = S.FT[fidx];
+    // deposits: into this zone's side(s) (fused), or both sides (face pass)
+    const bool depP = MODE == 1 ? F.z[1] >= 0 : (F.own & 1) != 0;
+    const bool depQ = MODE == 1 ? F.z[2] >= 0 : (F.own & 2) != 0;
     unsigned mask = 0;
     for (int k = 0; k < 4; ++k) if (F.z[k] >= 0) mask |= 1u << k;
-    if (F.own & 1) mask |= 1u << 4;
-    if (F.own & 2) mask |= 1u << 5;
+    if (depP) mask |= 1u << 4;
+    if (depQ) mask |= 1u << 5;
 
     // --- weights of the six remaps: slots 0..3 -> face, face -> slot 1, face -> slot 2
     const Loc<T>* LF = S.L + 5 * fidx;
@@ -1150,36 +1172,96 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
         if (sn == NS) { fn = next_face(fidx); sn = 0; }
         if (fn < nface) issue(fn, sn);
       }
-      if (tid == 0 && sizeof(T) == 4) {
+      if (MODE == 0 && tid == 0 && sizeof(T) == 4) {
         // exact total of this zone's deposits: (+sum F if own Q) - (sum F if own P)
         if (F.own & 2) S.dtot[s] = ff_add(S.dtot[s], sumF);
         if (F.own & 1) S.dtot[s] = ff_add(S.dtot[s], ff_neg(sumF));
       }
       // outflow tallies (number and energy at infinity)
+      double tn_sum = 0.0, te_sum = 0.0;
       if (outflow) {
-        double te_sum;
-        double tn_sum = block_sum2(tn, te, S.red, te_sum);
-        if (tid == 0) { S.tally[2 * s] += tn_sum; S.tally[2 * s + 1] += te_sum * F.al; }
+        tn_sum = block_sum2(tn, te, S.red, te_sum);
+        if (MODE == 0 && tid == 0) { S.tally[2 * s] += tn_sum; S.tally[2 * s + 1] += te_sum * F.al; }
+      }
+      if (MODE == 1 && tid == 0) {
+        // the receiving zones' records of this face: exact totals and tallies
+        const ff zero = ff{0.0f, 0.0f};
+        if (depP) {
+          DepRec& r = rec[((size_t)F.z[1] * 6 + 2 * F.axis + 1) * NS + s];
+          r.sum = sizeof(T) == 4 ? ff_neg(sumF) : zero;
+          r.tn = tn_sum; r.te = te_sum * F.al;
+        }
+        if (depQ) {
+          DepRec& r = rec[((size_t)F.z[2] * 6 + 2 * F.axis) * NS + s];
+          r.sum = sizeof(T) == 4 ? sumF : zero;
+          r.tn = depP ? 0.0 : tn_sum; r.te = depP ? 0.0 : te_sum * F.al;
+        }
       }
       // deposits into this zone: dN -= T_{s->P}[F] (own P), dN += T_{s->Q}[F] (own Q)
       T* EP = EB + 2 * nbin;
       T* EQ = EB + 3 * nbin;
       if (gact) {
-        if (F.own & 1) energy_column<T, T>(gc, nch, NE, NA, gb, em[4], ew[4], FL, EP, T(1), P3);
-        if (F.own & 2) energy_column<T, T>(gc, nch, NE, NA, gb, em[5], ew[5], FL, EQ, T(1), P3);
+        if (depP) energy_column<T, T>(gc, nch, NE, NA, gb, em[4], ew[4], FL, EP, T(1), P3);
+        if (depQ) energy_column<T, T>(gc, nch, NE, NA, gb, em[5], ew[5], FL, EQ, T(1), P3);
       }
       __syncthreads();
       if (gact) {
-        DN* dNs = S.dN + (size_t)s * nbin;
         const short* offP = S.off + 4 * (NA + 1);
         const short* offQ = S.off + 5 * (NA + 1);
-        if (F.own & 1)
-          angular_rows<T, T>(gc, nch, NE, NA, offP[gb], offP[gb + 1], S.ent + 4 * 4 * NA, EP, AddDN<T>{dNs, NA, gb, T(-1)});
-        if (F.own & 2)
-          angular_rows<T, T>(gc, nch, NE, NA, offQ[gb], offQ[gb + 1], S.ent + 5 * 4 * NA, EQ, AddDN<T>{dNs, NA, gb, T(1)});
+        if (MODE == 0) {
+          DN* dNs = S.dN + (size_t)s * nbin;
+          if (depP)
+            angular_rows<T, T>(gc, nch, NE, NA, offP[gb], offP[gb + 1], S.ent + 4 * 4 * NA, EP, AddDN<T>{dNs, NA, gb, T(-1)});
+          if (depQ)
+            angular_rows<T, T>(gc, nch, NE, NA, offQ[gb], offQ[gb + 1], S.ent + 5 * 4 * NA, EQ, AddDN<T>{dNs, NA, gb, T(1)});
+        } else {
+          if (depP) {
+            T* d = dep + (((size_t)F.z[1] * 6 + 2 * F.axis + 1) * NS + s) * nbin;
+            angular_rows<T, T>(gc, nch, NE, NA, offP[gb], offP[gb + 1], S.ent + 4 * 4 * NA, EP, StoreDep<T>{d, NA, gb, T(-1)});
+          }
+          if (depQ) {
+            T* d = dep + (((size_t)F.z[2] * 6 + 2 * F.axis) * NS + s) * nbin;
+            angular_rows<T, T>(gc, nch, NE, NA, offQ[gb], offQ[gb + 1], S.ent + 5 * 4 * NA, EQ, StoreDep<T>{d, NA, gb, T(1)});
+          }
+        }
       }
       __syncthreads();
     }
+  }
+
+  if constexpr (MODE == 1) return;   // the face pass ends here
+  if constexpr (MODE == 2) {
+    // gather this zone's deposits in the fused kernel's order: faces in
+    // order; per face the rows P side then Q side, the exact totals Q side
+    // then P side
+    for (int fidx = 0; fidx < nface; ++fidx) {
+      if (!face_exists(tb, a, b, fidx)) continue;
+      const int axis = fidx < 2 ? 0 : (fidx < 4 ? 1 : 2);
+      const bool isP = fidx == 1 || fidx == 3 || fidx == 4 || (fidx == 2 && tb.periodic_th);
+      const bool isQ = fidx == 0 || fidx == 4 || (fidx == 2);
+      const int slotP = 2 * axis + 1, slotQ = 2 * axis;
+      for (int s = 0; s < NS; ++s) {
+        DN* dNs = S.dN + (size_t)s * nbin;
+        for (int side = 0; side < 2; ++side) {
+          if (side == 0 ? !isP : !isQ) continue;
+          const T* src = dep + (((size_t)zone * 6 + (side == 0 ? slotP : slotQ)) * NS + s) * nbin;
+          for (int q = tid; q < nbin; q += NT) dNs[q] += (DN)src[q];
+        }
+        if (tid == 0) {
+          const DepRec* rP = isP ? rec + ((size_t)zone * 6 + slotP) * NS + s : nullptr;
+          const DepRec* rQ = isQ ? rec + ((size_t)zone * 6 + slotQ) * NS + s : nullptr;
+          if (sizeof(T) == 4) {
+            if (rQ) S.dtot[s] = ff_add(S.dtot[s], rQ->sum);
+            if (rP) S.dtot[s] = ff_add(S.dtot[s], rP->sum);
+          }
+          // an outflow face has one side; the other side's record holds 0
+          const double tn = (rP ? rP->tn : 0.0) + (rQ ? rQ->tn : 0.0);
+          const double te = (rP ? rP->te : 0.0) + (rQ ? rQ->te : 0.0);
+          if (tn != 0.0 || te != 0.0) { S.tally[2 * s] += tn; S.tally[2 * s + 1] += te; }
+        }
+      }
+    }
+    __syncthreads();
   }
 
   // --- mixed path: restore the exact deposit total of every species before
@@ -1373,6 +1455,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
     }
     st.qye[zone] = q * st.phase_norm;
   }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT) : 1)
+    k_flux_collide(Tables tb, State st, double dt) {
+  flux_body<T, NT, 0>(tb, st, dt, nullptr, nullptr);
+}
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT) : 1)
+    k_flux_faces(Tables tb, State st, double dt, T* dep, DepRec* rec) {
+  flux_body<T, NT, 1>(tb, st, dt, dep, rec);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_zone_collide(Tables tb, State st, double dt, T* dep, DepRec* rec) {
+  flux_body<T, 256, 2>(tb, st, dt, dep, rec);
 }
 
 // ---------------------------------------------------------------------------
@@ -1949,16 +2046,37 @@ __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const 
 
 template <typename T, int NT>
 int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) {
-  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, nullptr, nullptr);
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 0, nullptr, nullptr);
   k_flux_collide<T, NT><<<tb.n_zone, NT, sm, s>>>(tb, st, dt);
+  return (int)cudaGetLastError();
+}
+
+// split form: the face pass, then the zone pass (both one CTA per zone)
+template <typename T, int NT>
+int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void* rec, cudaStream_t s) {
+  size_t sm1 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 1, nullptr, nullptr);
+  k_flux_faces<T, NT><<<tb.n_zone, NT, sm1, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
+  return (int)cudaGetLastError();
+}
+template <typename T>
+int launch_zone_t(const Tables& tb, const State& st, double dt, void* dep, void* rec, cudaStream_t s) {
+  size_t sm2 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 256 / 32, 2, nullptr, nullptr);
+  k_zone_collide<T><<<tb.n_zone, 256, sm2, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
   return (int)cudaGetLastError();
 }
 
 template <typename T, int NT>
 int flux_occupancy_t(const Tables& tb) {
-  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, nullptr, nullptr);
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 0, nullptr, nullptr);
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_flux_collide<T, NT>, NT, sm) != cudaSuccess) return 0;
+  return blocks;
+}
+template <typename T, int NT>
+int split_occupancy_t(const Tables& tb) {
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 1, nullptr, nullptr);
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_flux_faces<T, NT>, NT, sm) != cudaSuccess) return 0;
   return blocks;
 }
 
@@ -1972,9 +2090,21 @@ int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
 }  // namespace
 
 size_t flux_smem_bytes(const Tables& tb, int mixed, int nt) {
-  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nt / 32, nullptr, nullptr)
-               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, nt / 32, nullptr, nullptr);
+  const int threads = nt & 0xFFFF;
+  if (nt & kShapeSplit) {
+    size_t a = mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 1, nullptr, nullptr)
+                     : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 1, nullptr, nullptr);
+    size_t b = mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, nullptr, nullptr)
+                     : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, nullptr, nullptr);
+    return a > b ? a : b;
+  }
+  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 0, nullptr, nullptr)
+               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 0, nullptr, nullptr);
 }
+size_t split_dep_bytes(const Tables& tb, int mixed) {
+  return (size_t)tb.n_zone * 6 * tb.n_s * tb.n_e * tb.n_ang * (mixed ? 4 : 8);
+}
+size_t split_rec_bytes(const Tables& tb) { return (size_t)tb.n_zone * 6 * tb.n_s * sizeof(DepRec); }
 size_t remap_smem_bytes(const Tables& tb, int mixed) {
   return mixed ? remap_smem_layout<float>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr)
                : remap_smem_layout<double>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
@@ -1993,6 +2123,12 @@ int prepare_kernels() {
   BT_SET((k_flux_collide<double, 128>));
   BT_SET((k_flux_collide<double, 256>));
   BT_SET((k_flux_collide<double, 512>));
+  BT_SET((k_flux_faces<float, 256>));
+  BT_SET((k_flux_faces<float, 512>));
+  BT_SET((k_flux_faces<double, 256>));
+  BT_SET((k_flux_faces<double, 512>));
+  BT_SET((k_zone_collide<float>));
+  BT_SET((k_zone_collide<double>));
   BT_SET((k_time_remap<float>));
   BT_SET((k_time_remap<double>));
   BT_SET(k_sur_table);
@@ -2001,6 +2137,13 @@ int prepare_kernels() {
 }
 
 int flux_occupancy(const Tables& tb, int mixed, int nt) {
+  if (nt & kShapeSplit) {
+    switch (nt & 0xFFFF) {
+      case 256: return mixed ? split_occupancy_t<float, 256>(tb) : split_occupancy_t<double, 256>(tb);
+      case 512: return mixed ? split_occupancy_t<float, 512>(tb) : split_occupancy_t<double, 512>(tb);
+      default: return 0;
+    }
+  }
   switch (nt) {
     case 128: return mixed ? flux_occupancy_t<float, 128>(tb) : flux_occupancy_t<double, 128>(tb);
     case 512: return mixed ? flux_occupancy_t<float, 512>(tb) : flux_occupancy_t<double, 512>(tb);
@@ -2015,13 +2158,26 @@ int max_optin_smem() {
   return v;
 }
 
-int launch_flux_collide(const Tables& tb, const State& st, double dt, int mixed, int nt, void* stream) {
+int launch_flux_collide(const Tables& tb, const State& st, double dt, int mixed, int nt, void* dep, void* rec,
+                        void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
+  if (nt & kShapeSplit) {
+    if (!dep || !rec) return (int)cudaErrorInvalidValue;
+    if ((nt & 0xFFFF) == 512)
+      return mixed ? launch_faces_t<float, 512>(tb, st, dt, dep, rec, s) : launch_faces_t<double, 512>(tb, st, dt, dep, rec, s);
+    return mixed ? launch_faces_t<float, 256>(tb, st, dt, dep, rec, s) : launch_faces_t<double, 256>(tb, st, dt, dep, rec, s);
+  }
   switch (nt) {
     case 128: return mixed ? launch_flux_t<float, 128>(tb, st, dt, s) : launch_flux_t<double, 128>(tb, st, dt, s);
     case 512: return mixed ? launch_flux_t<float, 512>(tb, st, dt, s) : launch_flux_t<double, 512>(tb, st, dt, s);
     default: return mixed ? launch_flux_t<float, 256>(tb, st, dt, s) : launch_flux_t<double, 256>(tb, st, dt, s);
   }
+}
+
+int launch_zone_collide(const Tables& tb, const State& st, double dt, int mixed, void* dep, void* rec, void* stream) {
+  if (!dep || !rec) return (int)cudaErrorInvalidValue;
+  cudaStream_t s = (cudaStream_t)stream;
+  return mixed ? launch_zone_t<float>(tb, st, dt, dep, rec, s) : launch_zone_t<double>(tb, st, dt, dep, rec, s);
 }
 
 int launch_time_remap(const Tables& tb, const State& st, int mixed, void* stream) {

@@ -1,0 +1,82 @@
+"""The split flux step (face pass + zone pass, every face computed once)
+against the fused one and against the oracle.  The split form gathers each
+zone's deposits in the fused form's order, so the two must agree bit for
+bit in both precisions."""
+import numpy as np
+import pytest
+
+from paper_2003_02845_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SPLIT = 0x10000
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2003_02845_gb300 import build, bt
+    build.build()
+    return bt
+
+
+def _cases():
+    sphere = W.homogeneous_sphere(n_r=13, n_e=3, n_mu=6, n_phi=4, dang=0.25)
+    sphere.f0 = np.random.default_rng(3).uniform(0, 1, sphere.f0.shape)
+    slab = W.slab_diffusion(kappa_s=30.0, dz=0.02, z_max=0.3, n_mu=6)
+    slab.f0 = slab.f0 * np.random.default_rng(8).uniform(0.5, 1.5, slab.f0.shape)
+    return {
+        "column": W.random_column(1, n_r=11, n_e=5, n_mu=6, n_phi=4, n_s=2),
+        "origin": sphere,
+        "2d": W.random_2d(4, n_r=9, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=2),
+        "2d_origin_ragged": W.random_2d(6, n_r=7, n_theta=3, n_e=3, n_mu=5, n_phi=7, n_s=1, r_min=0.0),
+        "slab": slab,
+    }
+
+
+def _run(gpu, p, precision, shape, steps, dt):
+    t = gpu.Transport(p, precision)
+    t.set_launch_shape(shape)
+    assert t.launch_shape == shape
+    t.set_background(p.backgrounds[0])
+    t.set_f(p.f0)
+    for k in range(steps):
+        if p.alternate and len(p.backgrounds) > 1:
+            t.set_background(p.backgrounds[(k + 1) % 2])
+        t.step(dt)
+    return t
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["column", "origin", "2d", "2d_origin_ragged", "slab"])
+def test_split_equals_fused(gpu, case, precision):
+    p = _cases()[case]
+    a = _run(gpu, p, precision, 256, 6, 0.004)
+    for shape in (SPLIT | 256, SPLIT | 512):
+        b = _run(gpu, p, precision, shape, 6, 0.004)
+        assert np.array_equal(a.get_f(), b.get_f())
+        for x, y in zip(a.moments(), b.moments()):
+            assert np.array_equal(x, y)
+        for x, y in zip(a.totals(), b.totals()):
+            assert np.array_equal(x, y)
+
+
+def test_split_fp64_matches_oracle(orc, gpu):
+    p = W.random_2d(5, n_r=9, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=2)
+    o, dt = orc.run(p, n_steps=8)
+    t = _run(gpu, p, "fp64", SPLIT | 256, 8, dt)
+    fo = o.get_f()
+    assert np.abs(t.get_f() - fo).sum() / np.abs(fo).sum() <= 1e-12
+
+
+def test_autotune_considers_split(gpu, tmp_path, monkeypatch):
+    monkeypatch.setenv("BT_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    p = W.random_2d(7, n_r=12, n_theta=6, n_e=4, n_mu=4, n_phi=6, n_s=2)
+    t = gpu.Transport(p, "mixed")
+    t.set_background(p.backgrounds[0])
+    t.set_f(p.f0)
+    nt = t.autotune(0.01)
+    assert nt in (128, 256, 512, SPLIT | 256, SPLIT | 512)
+    t.step(0.01)   # the chosen shape runs
