@@ -634,11 +634,13 @@ struct FluxSmem {
   ff* zd_f;
   float* zq_f;     // [nang] phi^6 u^0 dOmega / dt
   double* zrow;    // [ns][ne][5] collision moment partials
+  ff* rowk;        // [ns][ne][4] ka, ks, ka + ks, ka f_eq of each row (mixed solve)
   double* wr_r;    // [warps][nang] f* of the warp's collision row   (aliases buf)
   double* wr_i;    // [warps][nang] 1/D per warp row                 (aliases buf)
   double* red;     // [kMaxWarps * 2]
   double* tally;   // [ns][2] outflow N, E of this zone
   double* corr;    // [ns] exact-total correction of dN (mixed)
+  ff* corr_f;      // [ns] the same as a double-float
   int* corr_at;    // [ns]
   ff* dtot;        // [ns] exact total of the deposits (mixed)
   ff* redf;        // [kMaxWarps]
@@ -654,6 +656,7 @@ struct FluxSmem {
   T* dOm;          // [nang]
   T* dGam;         // [ne]
   T* rdGam;        // [ne] 1/dGamma
+  T* epsS;         // [ne] group centres
   T* mu;           // [nmu]
   T* u0s;          // [nang] face
   T* vns;          // [nang]
@@ -682,17 +685,20 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
   } while (0)
   BT_TAKE(bar, unsigned long long, 2);
   BT_TAKE(dN, typename DNT<T>::type, mode == 1 ? 0 : (size_t)ns * nbin);   // the face pass keeps no dN
-  BT_TAKE(zu0, double, nang);
-  BT_TAKE(ztau, double, nang);
-  BT_TAKE(zcn, double, nang);
-  BT_TAKE(zt_f, ff, nang);
-  BT_TAKE(zc_f, ff, nang);
-  BT_TAKE(zd_f, ff, nang);
-  BT_TAKE(zq_f, float, nang);
-  BT_TAKE(zrow, double, (size_t)ns * ne * 5);
+  const int nz_ang = mode == 1 ? 0 : nang;   // the collision's arrays: not in the face pass
+  BT_TAKE(zu0, double, nz_ang);
+  BT_TAKE(ztau, double, nz_ang);
+  BT_TAKE(zcn, double, nz_ang);
+  BT_TAKE(zt_f, ff, nz_ang);
+  BT_TAKE(zc_f, ff, nz_ang);
+  BT_TAKE(zd_f, ff, nz_ang);
+  BT_TAKE(zq_f, float, nz_ang);
+  BT_TAKE(zrow, double, mode == 1 ? 0 : (size_t)ns * ne * 5);
+  BT_TAKE(rowk, ff, mode == 1 ? 0 : (size_t)ns * ne * 4);
   BT_TAKE(red, double, kMaxWarps * 2);
   BT_TAKE(tally, double, ns * 2);
   BT_TAKE(corr, double, ns);
+  BT_TAKE(corr_f, ff, ns);
   BT_TAKE(corr_at, int, ns);
   BT_TAKE(dtot, ff, ns);
   BT_TAKE(redf, ff, kMaxWarps);
@@ -729,6 +735,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
   BT_TAKE(dOm, T, nang);
   BT_TAKE(dGam, T, ne);
   BT_TAKE(rdGam, T, ne);
+  BT_TAKE(epsS, T, ne);
   BT_TAKE(mu, T, nmu);
   BT_TAKE(u0s, T, nang);
   BT_TAKE(vns, T, nang);
@@ -898,7 +905,11 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
     S.dOm[q] = (T)tb.dOm[q];
   }
-  for (int q = tid; q < NE; q += NT) { S.dGam[q] = (T)tb.dGam[q]; S.rdGam[q] = (T)(1.0 / tb.dGam[q]); }
+  for (int q = tid; q < NE; q += NT) {
+    S.dGam[q] = (T)tb.dGam[q];
+    S.rdGam[q] = (T)(1.0 / tb.dGam[q]);
+    S.epsS[q] = (T)tb.eps[q];
+  }
   for (int q = tid; q < 2 * NE + 3; q += NT) S.p3[q] = (T)tb.p3[q];
   for (int q = tid; q < NS * 2; q += NT) S.tally[q] = 0.0;
   for (int q = tid; q < NS; q += NT) S.dtot[q] = ff{0.0f, 0.0f};
@@ -1057,7 +1068,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       if (gact) {
 #pragma unroll
         for (int slot = 0; slot < 4; ++slot)
-          if (F.z[slot] >= 0)
+          if (F.z[slot] >= 0 && (F.type == F_INTERNAL || slot == 1 || slot == 2))
             energy_column<T, T>(gc, nch, NE, NA, gb, em[slot], ew[slot], SRC + slot * nbin, EB + slot * nbin,
                                 cang[slot], P3);
       }
@@ -1065,8 +1076,13 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       // angular pass: g_k = T_{k->s}[n_k] as face distribution (into SRC)
       if (gact) {
         const T csb = S.cs[gb];
+        // the outer stencil cells feed only the upwind slope: P-1 where the
+        // bin moves P -> Q, Q+1 where it moves Q -> P, and only at interior
+        // faces; the other values are never read
+        const bool upb = S.vns[gb] >= T(0);
         for (int slot = 0; slot < 4; ++slot) {
           if (F.z[slot] < 0) continue;
+          if ((slot == 0 || slot == 3) && (F.type != F_INTERNAL || upb != (slot == 0))) continue;
           const short* off = S.off + slot * (NA + 1);
           StoreG<T> st_g{SRC + slot * nbin, csb, NA, gb};
           angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
@@ -1234,6 +1250,31 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     // gather this zone's deposits in the fused kernel's order: faces in
     // order; per face the rows P side then Q side, the exact totals Q side
     // then P side
+    int rows[8], nrow = 0;   // this zone's deposit slots in that order
+    for (int fidx = 0; fidx < nface; ++fidx) {
+      if (!face_exists(tb, a, b, fidx)) continue;
+      const int axis = fidx < 2 ? 0 : (fidx < 4 ? 1 : 2);
+      const bool isP = fidx == 1 || fidx == 3 || fidx == 4 || (fidx == 2 && tb.periodic_th);
+      const bool isQ = fidx == 0 || fidx == 4 || (fidx == 2);
+      if (isP) rows[nrow++] = 2 * axis + 1;
+      if (isQ) rows[nrow++] = 2 * axis;
+    }
+    for (int s = 0; s < NS; ++s) {
+      // all of an element's rows are loaded before they are summed in order
+      const T* base = dep + ((size_t)zone * 6 * NS + s) * nbin;
+      DN* dNs = S.dN + (size_t)s * nbin;
+      for (int q = tid; q < nbin; q += NT) {
+        T v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k < nrow) v[k] = base[(size_t)rows[k] * NS * nbin + q];
+        DN acc = DN(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k < nrow) acc += (DN)v[k];
+        dNs[q] = acc;
+      }
+    }
     for (int fidx = 0; fidx < nface; ++fidx) {
       if (!face_exists(tb, a, b, fidx)) continue;
       const int axis = fidx < 2 ? 0 : (fidx < 4 ? 1 : 2);
@@ -1241,12 +1282,6 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       const bool isQ = fidx == 0 || fidx == 4 || (fidx == 2);
       const int slotP = 2 * axis + 1, slotQ = 2 * axis;
       for (int s = 0; s < NS; ++s) {
-        DN* dNs = S.dN + (size_t)s * nbin;
-        for (int side = 0; side < 2; ++side) {
-          if (side == 0 ? !isP : !isQ) continue;
-          const T* src = dep + (((size_t)zone * 6 + (side == 0 ? slotP : slotQ)) * NS + s) * nbin;
-          for (int q = tid; q < nbin; q += NT) dNs[q] += (DN)src[q];
-        }
         if (tid == 0) {
           const DepRec* rP = isP ? rec + ((size_t)zone * 6 + slotP) * NS + s : nullptr;
           const DepRec* rQ = isQ ? rec + ((size_t)zone * 6 + slotQ) * NS + s : nullptr;
@@ -1283,6 +1318,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       if (tid == 0) {
         ff c = ff_add(S.dtot[s], ff_neg(tot));
         S.corr[s] = ff_to_d(c) / tb.dGam[at / NA];   // back to content per unit dGamma
+        S.corr_f[s] = ff_from_d(S.corr[s]);
         S.corr_at[s] = at;
       }
     }
@@ -1299,33 +1335,59 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     const double* v = st.v + 3 * zone;
     double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     double gz = 1.0 / sqrt(1.0 - v2);
-    for (int ang = tid; ang < NA; ang += NT) {
-      int j = ang / NPH, k = ang % NPH;
-      double nv = v[0] * tb.mu[j] + (v[1] * tb.cph[k] + v[2] * tb.sph[k]) * tb.smu[j];
-      double u0 = gz * (1.0 + nv);
-      S.zu0[ang] = u0;
-      S.ztau[ang] = alz * dt / u0;
-      S.zcn[ang] = 1.0 / (c6z * volz * u0 * tb.dOm[ang]);   // dN is per unit dGamma
-      S.zt_f[ang] = ff_from_d(S.ztau[ang]);
-      S.zc_f[ang] = ff_from_d(S.zcn[ang]);
-      S.zd_f[ang] = ff_from_d(tb.dOm[ang]);
-      S.zq_f[ang] = (float)(c6z * u0 * tb.dOm[ang] * rdt);
+    if constexpr (sizeof(T) == 8) {
+      for (int ang = tid; ang < NA; ang += NT) {
+        int j = ang / NPH, k = ang % NPH;
+        double nv = v[0] * tb.mu[j] + (v[1] * tb.cph[k] + v[2] * tb.sph[k]) * tb.smu[j];
+        double u0 = gz * (1.0 + nv);
+        S.zu0[ang] = u0;
+        S.ztau[ang] = alz * dt / u0;
+        S.zcn[ang] = 1.0 / (c6z * volz * u0 * tb.dOm[ang]);   // dN is per unit dGamma
+      }
+    } else {
+      // the mixed solve's per-angle constants in double-float: the two
+      // reciprocals per angle by Newton steps on the FP32 pipes instead of
+      // float64 divisions (GB300 runs float64 at 1/64 of the float32 rate)
+      const ff alzdt = ff_from_d(alz * dt);
+      const ff czone = ff_from_d(1.0 / (c6z * volz));
+      // per-row opacity constants, converted once by one thread per row
+      // (float64 work done by all 32 lanes of a row's warp costs 32x on the
+      // narrow float64 pipe)
+      for (int row = tid; row < NS * NE; row += NT) {
+        const size_t oz = ((size_t)(row / NE) * tb.n_zone + zone) * NE + row % NE;
+        const double ka = st.ka[oz], ks = st.ks[oz], fe = st.fe[oz];
+        S.rowk[4 * row] = ff_from_d(ka);
+        S.rowk[4 * row + 1] = ff_from_d(ks);
+        S.rowk[4 * row + 2] = ff_from_d(ka + ks);
+        S.rowk[4 * row + 3] = ff_from_d(ka * fe);
+      }
+      for (int ang = tid; ang < NA; ang += NT) {
+        int j = ang / NPH, k = ang % NPH;
+        double nv = v[0] * tb.mu[j] + (v[1] * tb.cph[k] + v[2] * tb.sph[k]) * tb.smu[j];
+        double u0 = gz * (1.0 + nv);
+        const ff ru0 = ff_recip(ff_from_d(u0));
+        const ff dom = ff_from_d(tb.dOm[ang]);
+        S.zt_f[ang] = ff_mul(alzdt, ru0);
+        S.zc_f[ang] = ff_mul(ff_mul(czone, ru0), ff_recip(dom));   // dN is per unit dGamma
+        S.zd_f[ang] = dom;
+        S.zq_f[ang] = (float)(c6z * u0 * tb.dOm[ang] * rdt);
+      }
     }
   }
   __syncthreads();
   for (int row = warp; row < NS * NE; row += (NT / 32)) {
     const int s = row / NE, i = row % NE;
-    const size_t oz = ((size_t)s * tb.n_zone + zone) * NE + i;
-    const double ka = st.ka[oz], ks = st.ks[oz], fe = st.fe[oz];
     const T* fz = fin + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
     const DN* dn = S.dN + (size_t)s * nbin + (size_t)i * NA;
     const int cat = S.corr_at[s] - i * NA;       // corrected bin of this row, if any
-    const double cval = S.corr[s];
     T* fo = fout + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
-    const double cdg = c6z * tb.dGam[i] * rdt;
     double mN = 0.0, mE = 0.0, mP0 = 0.0, mP1 = 0.0, mP2 = 0.0;
     int bad = 0;
     if constexpr (sizeof(T) == 8) {
+      const size_t oz = ((size_t)s * tb.n_zone + zone) * NE + i;
+      const double ka = st.ka[oz], ks = st.ks[oz], fe = st.fe[oz];
+      const double cval = S.corr[s];
+      const double cdg = c6z * tb.dGam[i] * rdt;
       const double kt = ka + ks, kafe = ka * fe;
       double* rr = S.wr_r + (size_t)warp * NA;
       double* ri = S.wr_i + (size_t)warp * NA;
@@ -1367,16 +1429,17 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       // mixed path: double-float (about 48-bit) arithmetic on the FP32 pipes
       // keeps the solve conservative to well below 1e-10 where float32 would
       // not, at a fraction of GB300's float64 cost
-      const ff ka_f = ff_from_d(ka), ks_f = ff_from_d(ks);
-      const ff kt_f = ff_from_d(ka + ks), kafe_f = ff_from_d(ka * fe);
+      const ff ka_f = S.rowk[4 * row], ks_f = S.rowk[4 * row + 1];
+      const ff kt_f = S.rowk[4 * row + 2], kafe_f = S.rowk[4 * row + 3];
       float* buf = reinterpret_cast<float*>(S.wr_r) + (size_t)warp * 4 * NA;   // fst.hi, fst.lo, iD.hi, iD.lo
       ff sr = ff{0.0f, 0.0f}, s1 = ff{0.0f, 0.0f};
+      const ff cval_f = S.corr_f[s];
       for (int ang = lane; ang < NA; ang += 32) {
         const ff tau = S.zt_f[ang];
         const ff zcn = S.zc_f[ang];
         const ff dom = S.zd_f[ang];
         ff dnv = ff{(float)dn[ang], 0.0f};
-        if (ang == cat) dnv = ff_add(dnv, ff_from_d(cval));
+        if (ang == cat) dnv = ff_add(dnv, cval_f);
         const ff fst = ff_add(ff{(float)fz[ang], 0.0f}, ff_mul(zcn, dnv));
         const ff r = ff_add(fst, ff_mul(tau, kafe_f));
         const ff iD = ff_recip(ff_add(ff{1.0f, 0.0f}, ff_mul(kt_f, tau)));
@@ -1394,8 +1457,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       const ff J = ff_mul(sr, ff_recip(s1));
       const ff ksJ = ff_mul(ks_f, J);
       float fN = 0.0f, fE = 0.0f, fP0 = 0.0f, fP1 = 0.0f, fP2 = 0.0f;
-      const float eps_i = (float)tb.eps[i];
-      const float dg_i = (float)tb.dGam[i];
+      const float eps_i = (float)S.epsS[i];
+      const float dg_i = (float)S.dGam[i];
       for (int ang = lane; ang < NA; ang += 32) {
         const ff tau = S.zt_f[ang];
         const ff fst = ff{buf[4 * ang], buf[4 * ang + 1]};
@@ -1414,15 +1477,26 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         fP1 += de * (float)S.n1[ang];
         fP2 += de * (float)S.n2[ang];
       }
+      // the lane sums are float32 already: reduce them in float32 too
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fN += __shfl_xor_sync(0xffffffffu, fN, o);
+        fE += __shfl_xor_sync(0xffffffffu, fE, o);
+        fP0 += __shfl_xor_sync(0xffffffffu, fP0, o);
+        fP1 += __shfl_xor_sync(0xffffffffu, fP1, o);
+        fP2 += __shfl_xor_sync(0xffffffffu, fP2, o);
+      }
       mN = fN; mE = fE; mP0 = fP0; mP1 = fP1; mP2 = fP2;
     }
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mN += __shfl_xor_sync(0xffffffffu, mN, o);
-      mE += __shfl_xor_sync(0xffffffffu, mE, o);
-      mP0 += __shfl_xor_sync(0xffffffffu, mP0, o);
-      mP1 += __shfl_xor_sync(0xffffffffu, mP1, o);
-      mP2 += __shfl_xor_sync(0xffffffffu, mP2, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        mN += __shfl_xor_sync(0xffffffffu, mN, o);
+        mE += __shfl_xor_sync(0xffffffffu, mE, o);
+        mP0 += __shfl_xor_sync(0xffffffffu, mP0, o);
+        mP1 += __shfl_xor_sync(0xffffffffu, mP1, o);
+        mP2 += __shfl_xor_sync(0xffffffffu, mP2, o);
+      }
     }
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
@@ -1462,8 +1536,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
     k_flux_collide(Tables tb, State st, double dt) {
   flux_body<T, NT, 0>(tb, st, dt, nullptr, nullptr);
 }
+// the face pass keeps no dN or collision arrays: in float32 four 256-thread
+// CTAs fit an SM (64 registers, no spills); 512-thread CTAs are for large
+// rows, where shared memory allows one or two per SM anyway
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT) : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 1024 / NT) : 1)
     k_flux_faces(Tables tb, State st, double dt, T* dep, DepRec* rec) {
   flux_body<T, NT, 1>(tb, st, dt, dep, rec);
 }
