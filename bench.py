@@ -130,14 +130,15 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one flux
-# launch from an ncu capture (profiles/k_flux_collide_*_config3.md), keyed by
+# launch from an ncu capture of this bench's small invocation, keyed by
 # workload, precision and launch shape, and valid only for the kernel source
 # it was taken on: a changed bt_kernels.cu reports null until re-captured.
+# For the split form the figure is the face pass plus the zone pass: f read
+# and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
-    ("config3_cc2d_256x64x12x80x3", "mixed", "fused/256"):
-        (371.97e6, "85cb2f212c7785ccc48af3435cf2633ee70ea9baa0f04b0f2a4a6a882c4041d2"),
-    ("config3_cc2d_256x64x12x80x3", "fp64", "fused/256"):
-        (755.74e6, "85cb2f212c7785ccc48af3435cf2633ee70ea9baa0f04b0f2a4a6a882c4041d2"),
+    ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
+        (210.45e6 + 1100.06e6 + 1337.84e6 + 180.23e6,
+         "9ec350dc8d1ee5f5afc3bb4c081839c61543ff5ef5957be9b656aa34fc6c8fab"),
 }
 
 
@@ -198,7 +199,9 @@ def run_ours(args):
     t.set_background(B[0])
     t.set_f(prob.f0)
     dt = t.max_dt(prob.cfl)
-    if args.autotune:
+    if args.shape:
+        t.set_launch_shape(parse_shape(args.shape))
+    elif args.autotune:
         t.autotune(dt)
     bins = prob.n_bins
     units_per_step = bins
@@ -331,7 +334,8 @@ def run_ours(args):
         ms64 = time_fp64_path(prob, dev)
         res["vs_fp64_gpu"] = {"value": units_per_step / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                               "speedup": ms64 / ms,
-                              "what": "the same step in plain FP64 on this GPU (same kernels, T = double)"}
+                              "what": "the same step in plain FP64 on this GPU (same kernels, T = double, "
+                                      "autotuned launch shape)"}
     if mixed and args.accuracy_steps > 0:
         f64 = run_steps(prob, dev, "fp64", args.accuracy_steps)
         res["accuracy"] = {"steps": args.accuracy_steps,
@@ -350,6 +354,13 @@ def run_ours(args):
         print(json.dumps(res), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def parse_shape(name):
+    """'fused/256' or 'split/512' -> the library's launch-shape code"""
+    from paper_2003_02845_gb300 import bt
+    form, nt = name.split("/")
+    return (bt.SHAPE_SPLIT if form == "split" else 0) | int(nt)
 
 
 def kernel_name(mixed, split):
@@ -453,6 +464,7 @@ def time_fp64_path(prob, dev, steps=5, warmup=3):
     t.set_background(prob.backgrounds[0])
     t.set_f(prob.f0)
     dt = t.max_dt(prob.cfl)
+    t.autotune(dt)          # its own best launch shape, as the timed path has
     for k in range(warmup):
         t.set_background_device(*dev[(k + 1) % 2])
         t.step(dt)
@@ -485,8 +497,13 @@ def run_batch(args, rank, world):
         m.set_f(p.f0)
         dts.append(m.max_dt(p.cfl))
     shapes = []
-    for m, d, dt in zip(b.members, dev, dts):
-        shapes.append(bt.shape_name(m.autotune(dt) if args.autotune else m.launch_shape))
+    fixed = args.shape.split(",") if args.shape else None
+    for i, (m, d, dt) in enumerate(zip(b.members, dev, dts)):
+        if fixed:
+            m.set_launch_shape(parse_shape(fixed[min(i, len(fixed) - 1)]))
+        elif args.autotune:
+            m.autotune(dt)
+        shapes.append(bt.shape_name(m.launch_shape))
     torch.cuda.synchronize()
     bins = sum(p.n_bins for p in probs)
 
@@ -723,6 +740,9 @@ def main():
     ap.add_argument("--sur-tols", type=float, nargs="+", default=[0.01, 0.05, 0.25])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing the candidates")
+    ap.add_argument("--shape", default=None,
+                    help="fixed launch shape, e.g. split/256 or fused/256 (no autotuning); for the batched "
+                         "workload a comma-separated list, one per problem")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
