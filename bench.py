@@ -108,6 +108,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over the ranks of the process group (the job's time is
+    its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def dist_init(n_gpus):
     import torch
     rank, world = 0, 1
@@ -228,9 +244,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = t.launch_count - l0
     if world > 1:
-        x = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        ms = float(x.item())
+        ms = max_over_ranks(ms)
         torch.distributed.barrier()
 
     # per-kernel durations with CUDA events on the transport stream
@@ -268,9 +282,7 @@ def run_ours(args):
         bt._check(L.bt_moments(t.h, bt.BT_MEM_HOST, *[x.data_ptr() for x in outs]))
     e2e_s = (time.perf_counter() - t0) / args.steps
     if world > 1:
-        x = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(x.item())
+        e2e_s = max_over_ranks(e2e_s)
 
     peaks, peak_src = load_peaks()
     bpb = algorithmic_bytes_per_bin(prob, mixed)
@@ -282,7 +294,7 @@ def run_ours(args):
     peak = hbm_peak(peaks)
     res = {
         "metric": METRIC,
-        "value": world * units_per_step / (ms * 1e-3),
+        "value": job_value(units_per_step, world, ms),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -529,9 +541,7 @@ def run_batch(args, rank, world):
     ms = ev0.elapsed_time(ev1) / args.steps
     launches, graphs = b.launch_count - l0, b.graph_launches - g0
     if world > 1:
-        x = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        ms = float(x.item())
+        ms = max_over_ranks(ms)
         torch.distributed.barrier()
 
     # end to end: pinned host backgrounds in, every member's source terms out
@@ -555,9 +565,7 @@ def run_batch(args, rank, world):
             bt._check(L.bt_moments(m.h, bt.BT_MEM_HOST, *[x.data_ptr() for x in o]))
     e2e_s = (time.perf_counter() - t0) / args.steps
     if world > 1:
-        x = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(x.item())
+        e2e_s = max_over_ranks(e2e_s)
 
     # the dominant kernel: the flux kernel of the largest member, timed alone
     big = max(range(len(probs)), key=lambda i: probs[i].n_bins)
@@ -581,7 +589,7 @@ def run_batch(args, rank, world):
     peak = hbm_peak(peaks)
     res = {
         "metric": METRIC,
-        "value": world * bins / (ms * 1e-3),
+        "value": job_value(bins, world, ms),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,

@@ -191,6 +191,7 @@ namespace {
 struct WsPlan {
   size_t tables[32];
   size_t bg[2][3], ka, ks, fe, f[2], mom_N, mom_E, mom_P, out_N, out_E, acc, red, flag, qye, tmp;
+  size_t ftab;   // float32 copies of the zone-independent tables
   size_t total;
 };
 
@@ -211,6 +212,7 @@ int plan(const bt_config* c, WsPlan& P, size_t* tab_sizes) {
     P.tables[i] = L.take(8 * sizes[i]);
   }
   P.tables[ntab] = L.take(4 * ns);  // species kinds
+  P.ftab = L.take(4 * ((size_t)c->n_mu + 4 * nang + 3 * ne + 2 * ne + 3));
   for (int s = 0; s < 2; ++s) {
     P.bg[s][0] = L.take(8 * 3 * nz);
     P.bg[s][1] = L.take(8 * nz);
@@ -462,6 +464,24 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
     if (e != cudaSuccess) { bt_destroy(h); return cuda_fail(e, "upload tables"); }
   }
   cudaMemcpyAsync(base + P.tables[ntab], h->kinds.data(), 4 * c->n_species, cudaMemcpyHostToDevice, h->stream);
+  // float32 copies for the mixed kernels, rounded from the same float64
+  // values the kernels would otherwise convert per CTA:
+  // [mu | n0 | n1 | n2 | dOmega | dGamma | 1/dGamma | eps | R^(3k)]
+  std::vector<float> ft;
+  ft.reserve((size_t)nmu + 4 * nang + 5 * ne + 3);
+  for (int j = 0; j < nmu; ++j) ft.push_back((float)mu[j]);
+  for (int q = 0; q < nang; ++q) ft.push_back((float)mu[q / nph]);
+  for (int q = 0; q < nang; ++q) ft.push_back((float)(smu[q / nph] * cph[q % nph]));
+  for (int q = 0; q < nang; ++q) ft.push_back((float)(smu[q / nph] * sph[q % nph]));
+  for (int q = 0; q < nang; ++q) ft.push_back((float)dOm[q]);
+  for (int i = 0; i < ne; ++i) ft.push_back((float)dGam[i]);
+  for (int i = 0; i < ne; ++i) ft.push_back((float)(1.0 / dGam[i]));
+  for (int i = 0; i < ne; ++i) ft.push_back((float)eps[i]);
+  for (int k = 0; k < 2 * ne + 3; ++k) ft.push_back((float)p3[k]);
+  {
+    cudaError_t e = cudaMemcpyAsync(base + P.ftab, ft.data(), 4 * ft.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { bt_destroy(h); return cuda_fail(e, "upload float tables"); }
+  }
 
   bt::Tables& T = h->tb;
   T.geom = c->geom; T.slab = slab; T.periodic_th = !slab && c->theta_periodic;
@@ -476,6 +496,18 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   T.G_r = D(P.tables[15]); T.G_t = D(P.tables[16]); T.G_p = D(P.tables[17]);
   T.p3 = D(P.tables[18]);
   T.species_kind = reinterpret_cast<const int*>(base + P.tables[ntab]);
+  {
+    const float* fb = reinterpret_cast<const float*>(base + P.ftab);
+    T.f_mu = fb; fb += nmu;
+    T.f_n0 = fb; fb += nang;
+    T.f_n1 = fb; fb += nang;
+    T.f_n2 = fb; fb += nang;
+    T.f_dOm = fb; fb += nang;
+    T.f_dGam = fb; fb += ne;
+    T.f_rdGam = fb; fb += ne;
+    T.f_eps = fb; fb += ne;
+    T.f_p3 = fb;
+  }
 
   for (int s = 0; s < 2; ++s)
     for (int q = 0; q < 3; ++q) h->bg[s][q] = D(P.bg[s][q]);

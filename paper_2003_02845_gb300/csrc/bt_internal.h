@@ -42,6 +42,10 @@ struct Tables {
   const double* G_t;     // [n_th + 1][4][9] stencil cell k -> polar face (column: [1][4][9])
   const double* G_p;     // [n_th][4][9]    periodic image k -> azimuthal face of row b
   const int* species_kind;
+  // float32 copies for the mixed-precision kernels (same roundings as a
+  // per-CTA conversion): mu [n_mu]; direction n0, n1, n2 and dOmega
+  // [n_ang]; dGamma, 1/dGamma, eps [n_e]; R^(3k) [2 n_e + 3]
+  const float *f_mu, *f_n0, *f_n1, *f_n2, *f_dOm, *f_dGam, *f_rdGam, *f_eps, *f_p3;
 };
 
 // Per-handle mutable device state.

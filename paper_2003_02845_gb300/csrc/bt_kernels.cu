@@ -894,23 +894,34 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   const unsigned rowbytes = (unsigned)(sizeof(T) * (size_t)nbin);
   const bool use_tma = (rowbytes % 16u) == 0u;
   unsigned tphase = 0;               // parity of the next mbarrier phase to wait for
+  const T dtT = (T)dt;               // converted once
 
   if (MODE != 1)
     for (int q = tid; q < NS * nbin; q += NT) S.dN[q] = DN(0);
-  for (int q = tid; q < NMU; q += NT) S.mu[q] = (T)tb.mu[q];
-  for (int q = tid; q < NA; q += NT) {
-    int j = q / NPH, k = q % NPH;
-    S.n0[q] = (T)tb.mu[j];
-    S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
-    S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
-    S.dOm[q] = (T)tb.dOm[q];
+  if constexpr (sizeof(T) == 4) {
+    // the float32 tables (no per-CTA float64 conversions)
+    for (int q = tid; q < NMU; q += NT) S.mu[q] = tb.f_mu[q];
+    for (int q = tid; q < NA; q += NT) {
+      S.n0[q] = tb.f_n0[q]; S.n1[q] = tb.f_n1[q]; S.n2[q] = tb.f_n2[q]; S.dOm[q] = tb.f_dOm[q];
+    }
+    for (int q = tid; q < NE; q += NT) { S.dGam[q] = tb.f_dGam[q]; S.rdGam[q] = tb.f_rdGam[q]; S.epsS[q] = tb.f_eps[q]; }
+    for (int q = tid; q < 2 * NE + 3; q += NT) S.p3[q] = tb.f_p3[q];
+  } else {
+    for (int q = tid; q < NMU; q += NT) S.mu[q] = (T)tb.mu[q];
+    for (int q = tid; q < NA; q += NT) {
+      int j = q / NPH, k = q % NPH;
+      S.n0[q] = (T)tb.mu[j];
+      S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
+      S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
+      S.dOm[q] = (T)tb.dOm[q];
+    }
+    for (int q = tid; q < NE; q += NT) {
+      S.dGam[q] = (T)tb.dGam[q];
+      S.rdGam[q] = (T)(1.0 / tb.dGam[q]);
+      S.epsS[q] = (T)tb.eps[q];
+    }
+    for (int q = tid; q < 2 * NE + 3; q += NT) S.p3[q] = (T)tb.p3[q];
   }
-  for (int q = tid; q < NE; q += NT) {
-    S.dGam[q] = (T)tb.dGam[q];
-    S.rdGam[q] = (T)(1.0 / tb.dGam[q]);
-    S.epsS[q] = (T)tb.eps[q];
-  }
-  for (int q = tid; q < 2 * NE + 3; q += NT) S.p3[q] = (T)tb.p3[q];
   for (int q = tid; q < NS * 2; q += NT) S.tally[q] = 0.0;
   for (int q = tid; q < NS; q += NT) S.dtot[q] = ff{0.0f, 0.0f};
   if (tid == 0) mbar_init(S.bar, 1);
@@ -1004,8 +1015,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         T vn = Ls.al / (Ls.cf * Ls.cf) * p[F.axis] / e;
         S.vns[ang] = vn;
         S.cs[ang] = T(1) / (ft.c6 * e * S.dOm[ang]);
-        S.taus[ang] = T(0.5) * (T)dt * ft.al / e;
-        S.vdx[ang] = T(0.5) * (T)dt * vn * ft.rdx;
+        S.taus[ang] = T(0.5) * dtT * ft.al / e;
+        S.vdx[ang] = T(0.5) * dtT * vn * ft.rdx;
       }
     }
     __syncthreads();
@@ -1136,7 +1147,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       const bool outflow = F.type == F_OUTFLOW_P || F.type == F_OUTFLOW_Q;
       if (gact) {
         const T vn = S.vns[gb];
-        const T fang = (T)dt * ft.area * ft.c6 * S.u0s[gb] * vn * S.dOm[gb];
+        const T fang = dtT * ft.area * ft.c6 * S.u0s[gb] * vn * S.dOm[gb];
         const int jj = gb / NPH, kk = gb % NPH;
         const int gm = (NMU - 1 - jj) * NPH + kk;   // mirror angle (reflecting wall)
         const bool up = vn >= T(0);
@@ -1554,7 +1565,7 @@ __global__ void __launch_bounds__(256) k_zone_collide(Tables tb, State st, doubl
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RemapSmem {
-  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3;
+  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3; T* fix;
   Wt<T>* W; AEnt<T>* ent; short* off; int* cnt;
   ff* redf; float* rkey; int* ridx;
 };
@@ -1571,6 +1582,7 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(src, T, (size_t)ne * nang);
   BT_TAKE(E, T, (size_t)ne * nang);
   BT_TAKE(dst, T, (size_t)ne * nang);
+  BT_TAKE(fix, T, 1);
   BT_TAKE(mu, T, nmu);
   BT_TAKE(n0, T, nang);
   BT_TAKE(n1, T, nang);
@@ -1601,16 +1613,25 @@ __global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
   const int nch = kThreads / NA > 0 ? kThreads / NA : 1;
   const int gb = tid % NA, gc = tid / NA;
   const bool gact = tid < nch * NA;
-  for (int q = tid; q < NMU; q += kThreads) S.mu[q] = (T)tb.mu[q];
-  for (int q = tid; q < NA; q += kThreads) {
-    int j = q / NPH, k = q % NPH;
-    S.n0[q] = (T)tb.mu[j];
-    S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
-    S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
-    S.dOm[q] = (T)tb.dOm[q];
+  if constexpr (sizeof(T) == 4) {
+    for (int q = tid; q < NMU; q += kThreads) S.mu[q] = tb.f_mu[q];
+    for (int q = tid; q < NA; q += kThreads) {
+      S.n0[q] = tb.f_n0[q]; S.n1[q] = tb.f_n1[q]; S.n2[q] = tb.f_n2[q]; S.dOm[q] = tb.f_dOm[q];
+    }
+    for (int q = tid; q < NE; q += kThreads) S.dGam[q] = tb.f_dGam[q];
+    for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = tb.f_p3[q];
+  } else {
+    for (int q = tid; q < NMU; q += kThreads) S.mu[q] = (T)tb.mu[q];
+    for (int q = tid; q < NA; q += kThreads) {
+      int j = q / NPH, k = q % NPH;
+      S.n0[q] = (T)tb.mu[j];
+      S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
+      S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
+      S.dOm[q] = (T)tb.dOm[q];
+    }
+    for (int q = tid; q < NE; q += kThreads) S.dGam[q] = (T)tb.dGam[q];
+    for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = (T)tb.p3[q];
   }
-  for (int q = tid; q < NE; q += kThreads) S.dGam[q] = (T)tb.dGam[q];
-  for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = (T)tb.p3[q];
   __syncthreads();
   const T* P3 = S.p3 + NE + 1;
   Loc<T> X, Y;
@@ -1664,15 +1685,20 @@ __global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
       }
       ff tot = block_sum_ff(partc, S.redf);
       at = block_argmax(bk, bi, S.rkey, S.ridx);
-      corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
+      // the corrected value of bin `at`, formed once (float64 work by every
+      // thread, or per bin, would run on GB300's narrow float64 pipe)
+      if (tid == 0) {
+        corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
+        S.fix[0] = (T)((double)S.dst[at] + corr_y);
+      }
+      __syncthreads();
     }
     if (gact) {
       const T u0 = Y.g * (T(1) + (Y.v[0] * S.n0[gb] + Y.v[1] * S.n1[gb] + Y.v[2] * S.n2[gb]));
       const T cang = c6y * u0 * S.dOm[gb];
       for (int ip = gc; ip < NE; ip += nch) {
         const int q = ip * NA + gb;
-        T d = S.dst[q];
-        if (q == at) d = (T)((double)d + corr_y);
+        const T d = q == at ? S.fix[0] : S.dst[q];
         fz[q] = d / cang;
       }
     }
