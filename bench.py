@@ -219,6 +219,7 @@ def run_ours(args):
         t.set_launch_shape(parse_shape(args.shape))
     elif args.autotune:
         t.autotune(dt)
+    shape = t.launch_shape
     bins = prob.n_bins
     units_per_step = bins
 
@@ -356,7 +357,7 @@ def run_ours(args):
                            "mixed_rel_l1": rel_l1(run_steps(prob, dev, "mixed", args.accuracy_steps), f64)}
         if args.learned_remap:
             try:
-                res["learned_remap"] = learned_remap_block(prob, dev, args, ms, f64)
+                res["learned_remap"] = learned_remap_block(prob, dev, args, ms, f64, shape)
             except Exception as e:   # report, do not lose the line
                 res["learned_remap"] = {"error": repr(e)}
         del f64
@@ -386,13 +387,15 @@ def rel_l1(a, b):
     return float((a.double() - b.double()).abs().sum() / b.double().abs().sum())
 
 
-def run_steps(prob, dev, precision, steps, sur=None, tol=0.0, stream=None):
+def run_steps(prob, dev, precision, steps, sur=None, tol=0.0, stream=None, shape=None):
     """f (device tensor) after `steps` steps from f0 with the backgrounds
     alternating as in the timed run, dt from the Courant limit of B0."""
     import torch
     from paper_2003_02845_gb300 import bt
     stream = stream if stream is not None else torch.cuda.Stream()
     t = bt.Transport(prob, precision, stream=stream)
+    if shape is not None:
+        t.set_launch_shape(shape)
     if sur is not None:
         t.set_surrogate(sur, tol)
     t.set_background(prob.backgrounds[0])
@@ -408,7 +411,7 @@ def run_steps(prob, dev, precision, steps, sur=None, tol=0.0, stream=None):
     return (f, stats) if sur is not None else f
 
 
-def learned_remap_block(prob, dev, args, ms_exact, f64):
+def learned_remap_block(prob, dev, args, ms_exact, f64, shape):
     """Train the network on rows of the exact remap from 16 seeded background
     pairs (the workload's own backgrounds are held out), then time the step
     with it and measure its error at a few trip tolerances."""
@@ -426,11 +429,12 @@ def learned_remap_block(prob, dev, args, ms_exact, f64):
     t2 = time.perf_counter()
     n_rows = int(X.shape[0])
     del X, Y
-    out = {"samples": n_rows, "epochs": args.sur_epochs, "batch": 4096,
+    out = {"samples": n_rows, "epochs": args.sur_epochs, "batch": 4096, "launch_shape": bt.shape_name(shape),
            "loss_per_epoch": [float(x) for x in log],
            "data_seconds": t1 - t0, "train_seconds": t2 - t1, "runs": []}
     for tol in args.sur_tols:
         t = bt.Transport(prob, "mixed", stream=stream)
+        t.set_launch_shape(shape)            # the exact run's launch shape
         net_s = net
         t.set_surrogate(net_s, tol)
         t.set_background(prob.backgrounds[0])
@@ -455,7 +459,8 @@ def learned_remap_block(prob, dev, args, ms_exact, f64):
         tab_ms, tab_n = t.profile_read(bt.K_SUR_TABLE)
         t.profile(False)
         t.close()
-        fs, (n_eval, n_trip) = run_steps(prob, dev, "mixed", args.accuracy_steps, sur=net_s, tol=tol, stream=stream)
+        fs, (n_eval, n_trip) = run_steps(prob, dev, "mixed", args.accuracy_steps, sur=net_s, tol=tol, stream=stream,
+                                         shape=shape)
         out["runs"].append({"tol_bins": tol, "ms_per_step": ms_sur, "value": prob.n_bins / (ms_sur * 1e-3),
                             "speed_vs_exact_mixed": ms_exact / ms_sur,
                             "table_kernel_ms": tab_ms / max(tab_n, 1),

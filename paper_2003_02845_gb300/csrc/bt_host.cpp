@@ -701,8 +701,9 @@ static int step_enqueue(bt_handle* h, double dt) {
   int e;
   if (h->sur) {
     ProfScope ps(h, BT_K_SUR_TABLE);
-    e = bt::launch_sur_table(h->tb, h->st, h->sur->prm, h->sur_tol, h->remap_pending ? 1 : 0, h->sur_tab,
-                             h->sur_counts, 4 * h->sur->n_sm, h->stream);
+    e = bt::launch_sur_table(h->tb, h->st, h->sur->prm, h->sur_tol, h->remap_pending ? 1 : 0,
+                             (h->nt & bt::kShapeSplit) ? 1 : 0, h->sur_tab, h->sur_counts, 4 * h->sur->n_sm,
+                             h->stream);
     h->launches += 1;
     if (e) return cuda_fail((cudaError_t)e, "learned remap table");
   }

@@ -104,10 +104,11 @@ int launch_check_finite(const Tables& T, const State& S, int mixed, void* stream
 // learned remap: features X [n][16], exact targets Y [n][27] and validity of
 // the rows idx [n][3] = (zone, kind, source angle)
 // learned remap: fill st.sur_tab with the network's weights (judged against
-// the exact ones; tripped rows take the exact weights).  counts [2]: rows
-// evaluated, rows tripped (uint64, accumulated).
-int launch_sur_table(const Tables& T, const State& S, const float* prm, float tol, int with_time, void* tab,
-                     unsigned long long* counts, int grid, void* stream);
+// the exact ones; tripped rows take the exact weights) for the rows the step
+// reads (split != 0: the split flux form, which reads only owned faces).
+// counts [2]: rows evaluated, rows tripped (uint64, accumulated).
+int launch_sur_table(const Tables& T, const State& S, const float* prm, float tol, int with_time, int split,
+                     void* tab, unsigned long long* counts, int grid, void* stream);
 size_t sur_table_bytes(const Tables& T);
 int launch_sur_samples(const Tables& T, const State& S, const int* idx, long long n, float* X, float* Y, int* valid,
                        void* stream);

@@ -1497,7 +1497,9 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         fP1 += __shfl_xor_sync(0xffffffffu, fP1, o);
         fP2 += __shfl_xor_sync(0xffffffffu, fP2, o);
       }
-      mN = fN; mE = fE; mP0 = fP0; mP1 = fP1; mP2 = fP2;
+      if (lane == 0) {   // converted by one lane only
+        mN = fN; mE = fE; mP0 = fP0; mP1 = fP1; mP2 = fP2;
+      }
     }
     if constexpr (sizeof(T) == 8) {
 #pragma unroll
@@ -2008,7 +2010,8 @@ constexpr size_t kSurH = kSurX + 4096;
 constexpr size_t kSurXf = kSurH + 16384;
 constexpr size_t kSurDir = kSurXf + ((sizeof(SurXfer) * kSurKindsAll + 127) & ~size_t(127));
 constexpr size_t kSurBar = kSurDir + 4 * (3 * kMaxAng + kMaxMu);
-constexpr size_t kSurBytes = kSurBar + 64;
+constexpr size_t kSurKl = kSurBar + 64;          // the zone's remap kinds to evaluate [32] + count
+constexpr size_t kSurBytes = kSurKl + 4 * 33;
 
 __device__ __forceinline__ float mean_offset(const float* p, int axis) {
   // sum over the 27 entries of offset * weight along one axis
@@ -2022,7 +2025,7 @@ __device__ __forceinline__ float mean_offset(const float* p, int axis) {
 }
 
 __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const float* __restrict__ prm, float tol,
-                                                     int with_time, Wt<float>* __restrict__ tab,
+                                                     int with_time, int split, Wt<float>* __restrict__ tab,
                                                      unsigned long long* counts) {
   extern __shared__ __align__(128) unsigned char smem[];
   const tc::MlpW w = tc::carve_w(smem);
@@ -2035,6 +2038,7 @@ __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const 
   float* smu = n2 + kMaxAng;
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + kSurBar);
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kSurBar + 8);
+  int* klist = reinterpret_cast<int*>(smem + kSurKl);
   const int t = threadIdx.x;
   const int NA = tb.n_ang, NPH = tb.n_ph, NMU = tb.n_mu;
   tc::stage_w(w, prm);
@@ -2055,13 +2059,15 @@ __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const 
   bool ok = true;
   unsigned long long n_eval = 0, n_trip = 0;
   const float Rf = (float)tb.R;
-  const int rows = kSurKindsAll * NA;
   for (int zone = blockIdx.x; zone < tb.n_zone && ok; zone += gridDim.x) {
     if (t < kSurKindsAll) {
       SurXfer& x = xf[t];
       FaceDesc F;
       RemapRow R;
-      x.ok = (t > 0 || with_time) && sur_row(tb, st, zone, t, F, R);
+      // rows the step reads: the time remap if pending; in the split form
+      // only the faces this zone owns (their other side reads them too)
+      const bool used = t == 0 ? with_time != 0 : (!split || face_owned(tb, zone % tb.n_r, (t - 1) / 6));
+      x.ok = used && sur_row(tb, st, zone, t, F, R);
       if (x.ok) {
         double f[16];
         sur_features(tb, R, 0, f);
@@ -2075,10 +2081,18 @@ __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const 
       }
     }
     __syncthreads();
+    if (t == 0) {   // compact list of the remaps that exist and are used
+      int nk = 0;
+      for (int k = 0; k < kSurKindsAll; ++k)
+        if (xf[k].ok) klist[nk++] = k;
+      klist[32] = nk;
+    }
+    __syncthreads();
+    const int rows = klist[32] * NA;
     for (int base = 0; base < rows && ok; base += kSurT) {
       const int q = base + t;
-      const int kind = q / NA, ang = q % NA;
-      const bool valid = q < rows && xf[kind].ok;
+      const bool valid = q < rows;
+      const int kind = valid ? klist[q / NA] : 0, ang = q % NA;
       float x[16], z[32], p[27];
       if (valid) {
         const SurXfer& X = xf[kind];
@@ -2324,10 +2338,10 @@ int launch_check_finite(const Tables&, const State&, int, void*) { return 0; }
 
 size_t sur_table_bytes(const Tables& tb) { return sizeof(Wt<float>) * (size_t)tb.n_zone * kSurKindsAll * tb.n_ang; }
 
-int launch_sur_table(const Tables& tb, const State& st, const float* prm, float tol, int with_time, void* tab,
-                     unsigned long long* counts, int grid, void* stream) {
+int launch_sur_table(const Tables& tb, const State& st, const float* prm, float tol, int with_time, int split,
+                     void* tab, unsigned long long* counts, int grid, void* stream) {
   const int g = grid < tb.n_zone ? grid : tb.n_zone;
-  k_sur_table<<<g, kSurT, kSurBytes, (cudaStream_t)stream>>>(tb, st, prm, tol, with_time,
+  k_sur_table<<<g, kSurT, kSurBytes, (cudaStream_t)stream>>>(tb, st, prm, tol, with_time, split,
                                                              reinterpret_cast<Wt<float>*>(tab), counts);
   return (int)cudaGetLastError();
 }

@@ -225,3 +225,16 @@ def test_config3_sampled(orc, gpu, precision, tol):
 def test_config2_full(orc, gpu, precision, tol):
     p = W.config2()
     compare_run(orc, gpu, p, 3, precision=precision, tol=tol)
+
+
+def test_gpu_size_limits(gpu):
+    # more angles than the kernels hold, and rows too long for shared memory,
+    # are refused at creation with an argument error (nothing is launched)
+    p = W.random_column(17, n_r=4, n_e=2, n_mu=17, n_phi=16, n_s=1)   # 272 angles > 256
+    with pytest.raises(gpu.BtError) as e:
+        gpu.Transport(p, "fp64")
+    assert e.value.code == -1
+    q = W.random_column(18, n_r=4, n_e=64, n_mu=16, n_phi=16, n_s=1)  # 16384 bins per row
+    with pytest.raises(gpu.BtError) as e:
+        gpu.Transport(q, "fp64")
+    assert e.value.code == -1 and "shared memory" in str(e.value)

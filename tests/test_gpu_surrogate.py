@@ -208,3 +208,29 @@ def test_learned_remap_step_conserves_and_counts(gpu):
     assert np.allclose(N + No, N0, rtol=1e-6, atol=0)
     n_eval, n_trip = t.sur_stats()
     assert n_eval > 0 and n_trip < n_eval      # the network is used on some rows
+
+
+def test_zero_tolerance_in_the_split_form(gpu):
+    # the split flux form reads only the rows of the faces each zone owns;
+    # the table is filled for exactly those
+    from paper_2003_02845_gb300 import workloads as W
+    p = W.random_2d(46, n_r=8, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=2)
+    s = gpu.Surrogate()
+    s.set_params(_params(8))
+
+    def run(sur):
+        t = gpu.Transport(p, "mixed")
+        t.set_launch_shape(gpu.SHAPE_SPLIT | 256)
+        if sur is not None:
+            t.set_surrogate(sur, 0.0)
+        t.set_background(p.backgrounds[0])
+        t.set_f(p.f0)
+        for k in range(4):
+            t.set_background(p.backgrounds[(k + 1) % 2])
+            t.step(0.01)
+        return t
+
+    a, b = run(None), run(s)
+    assert np.array_equal(a.get_f(), b.get_f())
+    n_eval, n_trip = b.sur_stats()
+    assert n_eval > 0 and n_trip == n_eval
