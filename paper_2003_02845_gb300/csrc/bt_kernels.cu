@@ -999,10 +999,11 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         if (sizeof(T) == 4 && st.sur_tab) {
           // learned remap: the table row of (zone, face fidx, remap r)
           w = reinterpret_cast<const Wt<T>*>(st.sur_tab)[((size_t)zone * kSurKindsAll + 1 + 6 * fidx + r) * NA + ang];
-        } else if (r < 4) {
-          chain_weights(tb, S.mu, S.n0, S.n1, S.n2, LF[slot], Ls, G, 0, F.axis, ang, Rg, w);
         } else {
-          chain_weights(tb, S.mu, S.n0, S.n1, S.n2, Ls, LF[slot], G, 1, F.axis, ang, Rg, w);
+          // one call site for both directions (cell -> face, face -> cell)
+          const bool back = r >= 4;
+          chain_weights(tb, S.mu, S.n0, S.n1, S.n2, back ? Ls : LF[slot], back ? LF[slot] : Ls, G, back ? 1 : 0,
+                        F.axis, ang, Rg, w);
         }
         S.W[r * NA + ang] = w;
       }
@@ -1227,28 +1228,29 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       // deposits into this zone: dN -= T_{s->P}[F] (own P), dN += T_{s->Q}[F] (own Q)
       T* EP = EB + 2 * nbin;
       T* EQ = EB + 3 * nbin;
+      // one code path for both sides (P first): a smaller kernel body
       if (gact) {
-        if (depP) energy_column<T, T>(gc, nch, NE, NA, gb, em[4], ew[4], FL, EP, T(1), P3);
-        if (depQ) energy_column<T, T>(gc, nch, NE, NA, gb, em[5], ew[5], FL, EQ, T(1), P3);
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side)
+          if (side == 0 ? depP : depQ)
+            energy_column<T, T>(gc, nch, NE, NA, gb, side == 0 ? em[4] : em[5], side == 0 ? ew[4] : ew[5], FL,
+                                side == 0 ? EP : EQ, T(1), P3);
       }
       __syncthreads();
       if (gact) {
-        const short* offP = S.off + 4 * (NA + 1);
-        const short* offQ = S.off + 5 * (NA + 1);
-        if (MODE == 0) {
-          DN* dNs = S.dN + (size_t)s * nbin;
-          if (depP)
-            angular_rows<T, T>(gc, nch, NE, NA, offP[gb], offP[gb + 1], S.ent + 4 * 4 * NA, EP, AddDN<T>{dNs, NA, gb, T(-1)});
-          if (depQ)
-            angular_rows<T, T>(gc, nch, NE, NA, offQ[gb], offQ[gb + 1], S.ent + 5 * 4 * NA, EQ, AddDN<T>{dNs, NA, gb, T(1)});
-        } else {
-          if (depP) {
-            T* d = dep + (((size_t)F.z[1] * 6 + 2 * F.axis + 1) * NS + s) * nbin;
-            angular_rows<T, T>(gc, nch, NE, NA, offP[gb], offP[gb + 1], S.ent + 4 * 4 * NA, EP, StoreDep<T>{d, NA, gb, T(-1)});
-          }
-          if (depQ) {
-            T* d = dep + (((size_t)F.z[2] * 6 + 2 * F.axis) * NS + s) * nbin;
-            angular_rows<T, T>(gc, nch, NE, NA, offQ[gb], offQ[gb + 1], S.ent + 5 * 4 * NA, EQ, StoreDep<T>{d, NA, gb, T(1)});
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+          if (!(side == 0 ? depP : depQ)) continue;
+          const short* off = S.off + (4 + side) * (NA + 1);
+          const AEnt<T>* ent = S.ent + (4 + side) * 4 * NA;
+          const T* Es = side == 0 ? EP : EQ;
+          const T sgn = side == 0 ? T(-1) : T(1);
+          if (MODE == 0) {
+            angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es,
+                               AddDN<T>{S.dN + (size_t)s * nbin, NA, gb, sgn});
+          } else {
+            T* d = dep + (((size_t)F.z[1 + side] * 6 + 2 * F.axis + (side == 0 ? 1 : 0)) * NS + s) * nbin;
+            angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn});
           }
         }
       }
