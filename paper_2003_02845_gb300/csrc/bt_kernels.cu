@@ -426,7 +426,24 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
 // clamp(i+m) (weight 1-we) and clamp(i+m+1) (we), and its content per unit
 // dGamma is rescaled by dGamma_i / dGamma_t = R^(3(i-t)) (p3c[k] = R^(3k)):
 //   E[t] = c * sum_i w(t|i) R^(3(i-t)) src[i].
+// the first and last group's rows (clamped targets): a separate, not inlined
+// function keeps the hot loop of the flux kernel small (its instruction
+// fetch stalls otherwise; the same rows, the same sums)
 template <typename T, typename A>
+__device__ __noinline__ A energy_edge(int t, int ne, int na, int b, int m, A wl, A wr, const T* src, const T* p3c) {
+  A acc = A(0);
+  int lo = (t == 0) ? 0 : t - m;
+  int hi = (t == ne - 1) ? ne - 1 : t - m;
+  lo = max(lo, 0); hi = min(hi, ne - 1);
+  for (int i = lo; i <= hi; ++i) acc += wl * (A)p3c[i - t] * (A)src[i * na + b];
+  lo = (t == 0) ? 0 : t - m - 1;
+  hi = (t == ne - 1) ? ne - 1 : t - m - 1;
+  lo = max(lo, 0); hi = min(hi, ne - 1);
+  for (int i = lo; i <= hi; ++i) acc += wr * (A)p3c[i - t] * (A)src[i * na + b];
+  return acc;
+}
+
+template <typename T, typename A, bool kEdgeCall = false>
 __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, int b, int m, T we, const T* src, T* E,
                                               T c, const T* p3c) {
   const A wl = (A)c * (A(1) - (A)we), wr = (A)c * (A)we;
@@ -439,6 +456,8 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
       int iL = t - m, iR = t - m - 1;
       if (iL >= 0 && iL < ne) acc += wli * (A)src[iL * na + b];
       if (iR >= 0 && iR < ne) acc += wri * (A)src[iR * na + b];
+    } else if (kEdgeCall) {
+      acc = energy_edge<T, A>(t, ne, na, b, m, wl, wr, src, p3c);
     } else {
       int lo = (t == 0) ? 0 : t - m;
       int hi = (t == ne - 1) ? ne - 1 : t - m;
@@ -1081,7 +1100,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
 #pragma unroll
         for (int slot = 0; slot < 4; ++slot)
           if (F.z[slot] >= 0 && (F.type == F_INTERNAL || slot == 1 || slot == 2))
-            energy_column<T, T>(gc, nch, NE, NA, gb, em[slot], ew[slot], SRC + slot * nbin, EB + slot * nbin,
+            energy_column<T, T, true>(gc, nch, NE, NA, gb, em[slot], ew[slot], SRC + slot * nbin, EB + slot * nbin,
                                 cang[slot], P3);
       }
       __syncthreads();
@@ -1233,7 +1252,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
 #pragma unroll 1
         for (int side = 0; side < 2; ++side)
           if (side == 0 ? depP : depQ)
-            energy_column<T, T>(gc, nch, NE, NA, gb, side == 0 ? em[4] : em[5], side == 0 ? ew[4] : ew[5], FL,
+            energy_column<T, T, true>(gc, nch, NE, NA, gb, side == 0 ? em[4] : em[5], side == 0 ? ew[4] : ew[5], FL,
                                 side == 0 ? EP : EQ, T(1), P3);
       }
       __syncthreads();
