@@ -153,8 +153,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (210.45e6 + 1100.06e6 + 1337.84e6 + 180.23e6,
-         "9ec350dc8d1ee5f5afc3bb4c081839c61543ff5ef5957be9b656aa34fc6c8fab"),
+        (206.58e6 + 1098.96e6 + 1337.86e6 + 180.18e6,
+         "95f8b33ff98b709a94c0386572a30a5f66dc1604c0f3bd6480ded2cfb126b5bc"),
 }
 
 
