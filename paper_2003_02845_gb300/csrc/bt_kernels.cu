@@ -1518,8 +1518,9 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         fP1 += __shfl_xor_sync(0xffffffffu, fP1, o);
         fP2 += __shfl_xor_sync(0xffffffffu, fP2, o);
       }
-      if (lane == 0) {   // converted by one lane only
-        mN = fN; mE = fE; mP0 = fP0; mP1 = fP1; mP2 = fP2;
+      if (lane == 0) {   // float32 row partials; summed per species below
+        float* zf = reinterpret_cast<float*>(S.zrow) + (size_t)row * 5;
+        zf[0] = fN; zf[1] = fE; zf[2] = fP0; zf[3] = fP1; zf[4] = fP2;
       }
     }
     if constexpr (sizeof(T) == 8) {
@@ -1534,16 +1535,28 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     }
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
-      double* zr = S.zrow + (size_t)row * 5;
-      zr[0] = mN; zr[1] = mE; zr[2] = mP0; zr[3] = mP1; zr[4] = mP2;
+      if constexpr (sizeof(T) == 8) {
+        double* zr = S.zrow + (size_t)row * 5;
+        zr[0] = mN; zr[1] = mE; zr[2] = mP0; zr[3] = mP1; zr[4] = mP2;
+      }
       if (bad) st.flag[0] = 1;
     }
   }
   __syncthreads();
   for (int s = tid; s < NS; s += NT) {
     double m[5] = {0, 0, 0, 0, 0};
-    for (int i = 0; i < NE; ++i)
-      for (int c = 0; c < 5; ++c) m[c] += S.zrow[((size_t)s * NE + i) * 5 + c];
+    if constexpr (sizeof(T) == 8) {
+      for (int i = 0; i < NE; ++i)
+        for (int c = 0; c < 5; ++c) m[c] += S.zrow[((size_t)s * NE + i) * 5 + c];
+    } else {
+      // double-float sums of the float32 row partials, converted once
+      const float* zf = reinterpret_cast<const float*>(S.zrow);
+      ff acc[5] = {ff{0.0f, 0.0f}, ff{0.0f, 0.0f}, ff{0.0f, 0.0f}, ff{0.0f, 0.0f}, ff{0.0f, 0.0f}};
+      for (int i = 0; i < NE; ++i)
+        for (int c = 0; c < 5; ++c) acc[c] = ff_add(acc[c], zf[((size_t)s * NE + i) * 5 + c]);
+      for (int c = 0; c < 5; ++c) m[c] = ff_to_d(acc[c]);
+    }
+    S.corr[s] = m[0];   // the species' number source (the correction is spent)
     size_t o = (size_t)s * tb.n_zone + zone;
     st.mom_N[o] = m[0];
     st.mom_E[o] = m[1];
@@ -1551,14 +1564,14 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     st.out_N[o] = S.tally[2 * s];
     st.out_E[o] = S.tally[2 * s + 1];
   }
+  __syncthreads();
   if (tid == 0) {
     // Q_Ye = -(dN_nue - dN_nuebar) / h^3 (Eq. hydrosource)
     double q = 0.0;
     for (int s = 0; s < NS; ++s) {
       int kind = tb.species_kind[s];
       if (kind != 0 && kind != 1) continue;
-      double m = 0.0;
-      for (int i = 0; i < NE; ++i) m += S.zrow[((size_t)s * NE + i) * 5];
+      const double m = S.corr[s];
       q += kind == 0 ? -m : m;
     }
     st.qye[zone] = q * st.phase_norm;
