@@ -1291,22 +1291,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       if (isP) rows[nrow++] = 2 * axis + 1;
       if (isQ) rows[nrow++] = 2 * axis;
     }
-    for (int s = 0; s < NS; ++s) {
-      // all of an element's rows are loaded before they are summed in order
-      const T* base = dep + ((size_t)zone * 6 * NS + s) * nbin;
-      DN* dNs = S.dN + (size_t)s * nbin;
-      for (int q = tid; q < nbin; q += NT) {
-        T v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < nrow) v[k] = base[(size_t)rows[k] * NS * nbin + q];
-        DN acc = DN(0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < nrow) acc += (DN)v[k];
-        dNs[q] = acc;
-      }
-    }
+    // exact totals and outflow tallies of the zone's records
     for (int fidx = 0; fidx < nface; ++fidx) {
       if (!face_exists(tb, a, b, fidx)) continue;
       const int axis = fidx < 2 ? 0 : (fidx < 4 ? 1 : 2);
@@ -1328,12 +1313,48 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         }
       }
     }
+    for (int s = 0; s < NS; ++s) {
+      // all of an element's rows are loaded before they are summed in order;
+      // the mixed path's exact-total correction is found in the same pass
+      const T* base = dep + ((size_t)zone * 6 * NS + s) * nbin;
+      DN* dNs = S.dN + (size_t)s * nbin;
+      ff part = ff{0.0f, 0.0f};
+      float bk = -1.0f;
+      int bi = 0x7fffffff;
+      for (int q = tid; q < nbin; q += NT) {
+        T v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k < nrow) v[k] = base[(size_t)rows[k] * NS * nbin + q];
+        DN acc = DN(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k < nrow) acc += (DN)v[k];
+        dNs[q] = acc;
+        if (sizeof(T) == 4) {
+          const float c = (float)acc * (float)S.dGam[q / NA];
+          part = ff_add(part, two_prod((float)acc, (float)S.dGam[q / NA]));
+          const float k = fabsf(c);
+          if (k > bk) { bk = k; bi = q; }
+        }
+      }
+      if (sizeof(T) == 4) {
+        ff tot = block_sum_ff(part, S.redf);
+        int at = block_argmax(bk, bi, S.rkey, S.ridx);
+        if (tid == 0) {
+          ff c = ff_add(S.dtot[s], ff_neg(tot));
+          S.corr[s] = ff_to_d(c) / tb.dGam[at / NA];   // back to content per unit dGamma
+          S.corr_f[s] = ff_from_d(S.corr[s]);
+          S.corr_at[s] = at;
+        }
+      }
+    }
     __syncthreads();
   }
 
   // --- mixed path: restore the exact deposit total of every species before
   //     the collision (float accumulation rounds; number must not drift)
-  if (sizeof(T) == 4) {
+  if (sizeof(T) == 4 && MODE != 2) {   // (the zone pass found it while gathering)
     for (int s = 0; s < NS; ++s) {
       const DN* dNs = S.dN + (size_t)s * nbin;
       ff part = ff{0.0f, 0.0f};
@@ -1354,7 +1375,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         S.corr_at[s] = at;
       }
     }
-  } else {
+  } else if (sizeof(T) == 8) {
     for (int s = tid; s < NS; s += NT) { S.corr[s] = 0.0; S.corr_at[s] = -1; }
   }
 
