@@ -1211,8 +1211,19 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           }
         }
       }
-      if (sizeof(T) == 4) sumF = block_sum_ff(sumF, S.redf);
-      else __syncthreads();
+      // the block's exact flux total, needed by thread 0 only: warp sums now,
+      // their sum after the barrier the deposits need anyway
+      if (sizeof(T) == 4) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sumF = ff_add(sumF, ff_shfl_down(sumF, o));
+        if (lane == 0) S.redf[warp] = sumF;
+      }
+      __syncthreads();
+      if (sizeof(T) == 4 && tid == 0) {
+        ff t = S.redf[0];
+        for (int w = 1; w < NT / 32; ++w) t = ff_add(t, S.redf[w]);
+        sumF = t;
+      }
       // the stencil buffers are free: prefetch the next rows while depositing
       {
         int fn = fidx, sn = s + 1;
