@@ -153,8 +153,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (206.58e6 + 1098.96e6 + 1337.86e6 + 180.18e6,
-         "95f8b33ff98b709a94c0386572a30a5f66dc1604c0f3bd6480ded2cfb126b5bc"),
+        (207.87e6 + 1098.65e6 + 1337.83e6 + 180.50e6,
+         "97a4679c3ab4ceae8ba0bf1eefefd2ff24ea7b1225c47293b3df105237dfdd3f"),
 }
 
 
