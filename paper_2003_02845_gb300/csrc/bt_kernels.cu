@@ -663,6 +663,9 @@ struct FluxSmem {
   int* corr_at;    // [ns]
   ff* dtot;        // [ns] exact total of the deposits (mixed)
   ff* redf;        // [kMaxWarps]
+  ff* redfS;       // [ns][kMaxWarps] per-species warp sums (zone pass)
+  float* rkeyS;    // [ns][kMaxWarps]
+  int* ridxS;      // [ns][kMaxWarps]
   float* rkey;     // [kMaxWarps]
   int* ridx;       // [kMaxWarps]
   unsigned long long* bar;  // mbarrier of the stencil copies
@@ -721,6 +724,9 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
   BT_TAKE(corr_at, int, ns);
   BT_TAKE(dtot, ff, ns);
   BT_TAKE(redf, ff, kMaxWarps);
+  BT_TAKE(redfS, ff, mode == 2 ? (size_t)ns * kMaxWarps : 0);
+  BT_TAKE(rkeyS, float, mode == 2 ? (size_t)ns * kMaxWarps : 0);
+  BT_TAKE(ridxS, int, mode == 2 ? (size_t)ns * kMaxWarps : 0);
   BT_TAKE(rkey, float, kMaxWarps);
   BT_TAKE(ridx, int, kMaxWarps);
   {
@@ -1350,17 +1356,41 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         }
       }
       if (sizeof(T) == 4) {
-        ff tot = block_sum_ff(part, S.redf);
-        int at = block_argmax(bk, bi, S.rkey, S.ridx);
-        if (tid == 0) {
-          ff c = ff_add(S.dtot[s], ff_neg(tot));
-          S.corr[s] = ff_to_d(c) / tb.dGam[at / NA];   // back to content per unit dGamma
-          S.corr_f[s] = ff_from_d(S.corr[s]);
-          S.corr_at[s] = at;
+        // warp reductions now; the block's, for every species, after one
+        // barrier below (same order of operations as a block reduction)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          part = ff_add(part, ff_shfl_down(part, o));
+          const float k2 = __shfl_down_sync(0xffffffffu, bk, o);
+          const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+          if (k2 > bk || (k2 == bk && i2 < bi)) { bk = k2; bi = i2; }
+        }
+        if (lane == 0) {
+          S.redfS[s * kMaxWarps + warp] = part;
+          S.rkeyS[s * kMaxWarps + warp] = bk;
+          S.ridxS[s * kMaxWarps + warp] = bi;
         }
       }
     }
     __syncthreads();
+    if (sizeof(T) == 4) {
+      for (int s = tid; s < NS; s += NT) {
+        ff tot = S.redfS[s * kMaxWarps];
+        float kb = S.rkeyS[s * kMaxWarps];
+        int at = S.ridxS[s * kMaxWarps];
+        for (int w = 1; w < NT / 32; ++w) {
+          tot = ff_add(tot, S.redfS[s * kMaxWarps + w]);
+          const float k2 = S.rkeyS[s * kMaxWarps + w];
+          const int i2 = S.ridxS[s * kMaxWarps + w];
+          if (k2 > kb || (k2 == kb && i2 < at)) { kb = k2; at = i2; }
+        }
+        ff c = ff_add(S.dtot[s], ff_neg(tot));
+        S.corr[s] = ff_to_d(c) / tb.dGam[at / NA];   // back to content per unit dGamma
+        S.corr_f[s] = ff_from_d(S.corr[s]);
+        S.corr_at[s] = at;
+      }
+      __syncthreads();
+    }
   }
 
   // --- mixed path: restore the exact deposit total of every species before
