@@ -210,7 +210,6 @@ __device__ __forceinline__ void chain_weights(const Tables& tb, const T* s_mu, c
 struct ff {
   float hi, lo;
 };
-__device__ __forceinline__ ff ff_make(float a) { return ff{a, 0.0f}; }
 // error-free sum of two floats (Knuth's TwoSum)
 __device__ __forceinline__ ff two_sum(float a, float b) {
   float s = a + b;
@@ -474,28 +473,16 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
 
 // Angular pass for destination angle bp over the rows of this thread:
 // out(t) = sum_e w_e E[t][b_e]; the list (at most 8 entries kept in registers,
-// longer lists streamed) is read once for all rows.
+// longer lists streamed) is read once for all rows.  The lanes of a warp run
+// the register path together up to the longest list among them (lanes with
+// shorter lists skip the extra entries), so lists of uneven length do not
+// split the warp into separate passes.
 template <typename T, typename A, typename Out>
 __device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int e0, int e1, const AEnt<T>* ent,
                                              const T* E, Out out) {
   const int n = e1 - e0;
-  if (n <= 4) {
-    T w[4];
-    int bb[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (k < n) { w[k] = ent[e0 + k].w; bb[k] = ent[e0 + k].b; }
-      else { w[k] = T(0); bb[k] = 0; }
-    }
-    for (int t = gc; t < ne; t += nch) {
-      const T* Er = E + t * na;
-      A acc = A(0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < n) acc += (A)w[k] * (A)Er[bb[k]];
-      out(t, acc);
-    }
-  } else if (n <= 8) {
+  const int nmax = __reduce_max_sync(__activemask(), n);
+  if (nmax <= 8) {
     T w[8];
     int bb[8];
 #pragma unroll
@@ -507,8 +494,10 @@ __device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, in
       const T* Er = E + t * na;
       A acc = A(0);
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
+      for (int k = 0; k < 8; ++k) {
+        if (k >= nmax) break;
         if (k < n) acc += (A)w[k] * (A)Er[bb[k]];
+      }
       out(t, acc);
     }
   } else {
@@ -1116,10 +1105,14 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         // the outer stencil cells feed only the upwind slope: P-1 where the
         // bin moves P -> Q, Q+1 where it moves Q -> P, and only at interior
         // faces; the other values are never read
+        // (one pass serves both outer cells: each lane takes the one its bin
+        // needs, so the warp does not run the two as separate passes)
         const bool upb = S.vns[gb] >= T(0);
-        for (int slot = 0; slot < 4; ++slot) {
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) {
+          const int slot = k == 0 ? (upb ? 0 : 3) : k;
           if (F.z[slot] < 0) continue;
-          if ((slot == 0 || slot == 3) && (F.type != F_INTERNAL || upb != (slot == 0))) continue;
+          if (k == 0 && F.type != F_INTERNAL) continue;
           const short* off = S.off + slot * (NA + 1);
           StoreG<T> st_g{SRC + slot * nbin, csb, NA, gb};
           angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
