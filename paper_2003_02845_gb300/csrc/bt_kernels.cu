@@ -323,98 +323,93 @@ struct AEnt {
   int b;   // source angle
 };
 
-// distinct angular targets of one source angle and their weights
+// the angular targets of one source angle in four fixed slots (mu bracket
+// lower/upper x Phi bracket lower/upper); a slot whose weight is zero, or
+// that repeats another slot's target on a one-node axis (its weight merged
+// there), is absent: tgt = -1
 template <typename T>
-__device__ __forceinline__ int ang_targets(const Wt<T>& W, int nmu, int nph, int* tgt, T* wa) {
+__device__ __forceinline__ void ang_targets4(const Wt<T>& W, int nmu, int nph, int* tgt, T* wa) {
   const int jL = W.jL, kL = W.kL;
   const int jR = nmu >= 2 ? jL + 1 : jL;
   const int kR = nph >= 2 ? (kL + 1) % nph : kL;
-  const T mj[2] = {T(1) - W.wmu, W.wmu};
-  const T mk[2] = {T(1) - W.wph, W.wph};
-  int n = 0;
-  for (int dj = 0; dj < 2; ++dj) {
-    int jt = dj ? jR : jL;
-    for (int dk = 0; dk < 2; ++dk) {
-      int kt = dk ? kR : kL;
-      int t = jt * nph + kt;
-      T w = mj[dj] * mk[dk];
-      if (w == T(0)) continue;        // adds nothing: keep the lists short
-      int q = 0;
-      while (q < n && tgt[q] != t) ++q;
-      if (q == n) { tgt[n] = t; wa[n] = w; ++n; }
-      else wa[q] += w;
-    }
-  }
-  return n;
+  const T mj0 = T(1) - W.wmu, mj1 = W.wmu;
+  const T mk0 = T(1) - W.wph, mk1 = W.wph;
+  wa[0] = mj0 * mk0; wa[1] = mj0 * mk1; wa[2] = mj1 * mk0; wa[3] = mj1 * mk1;
+  tgt[0] = jL * nph + kL; tgt[1] = jL * nph + kR; tgt[2] = jR * nph + kL; tgt[3] = jR * nph + kR;
+  if (kR == kL) { wa[0] += wa[1]; wa[1] = T(0); wa[2] += wa[3]; wa[3] = T(0); }
+  if (jR == jL) { wa[0] += wa[2]; wa[2] = T(0); wa[1] += wa[3]; wa[3] = T(0); }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (wa[k] == T(0)) tgt[k] = -1;   // adds nothing: keep the lists short
 }
 
-// Build the angular lists of the remaps whose bit is set in `mask`.
-// off: [nr][na+1], cnt: [nr][na] int scratch, ent: [nr][4 na].  Whole block.
+// Build the angular lists of the remaps whose bit is set in `mask`, each
+// destination's list sorted by source angle.  Every (remap, source) thread
+// sets its bit in a per-destination bitmask of sources (atomicOr: the result
+// does not depend on the order), the offsets are a scan of the masks' bit
+// counts, and an entry's place in its list is the number of lower sources in
+// the mask: no sorting pass, and all threads take part.
+// off: [nr][na+1], msk: [nr][na][ceil(na/32)] scratch, ent: [nr][4 na].
+// Whole block (synchronises at the end).
 template <typename T>
 __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int nmu, int nph, short* off,
-                             int* cnt, AEnt<T>* ent) {
-  const int tid = threadIdx.x;
-  for (int q = tid; q < nr * na; q += (int)blockDim.x) cnt[q] = 0;
+                             unsigned* msk, AEnt<T>* ent) {
+  const int tid = threadIdx.x, nt = (int)blockDim.x;
+  const int nwd = (na + 31) >> 5;
+  for (int q = tid; q < nr * na * nwd; q += nt) msk[q] = 0u;
   __syncthreads();
-  for (int q = tid; q < nr * na; q += (int)blockDim.x) {
-    int r = q / na, b = q % na;
+  for (int q = tid; q < nr * na; q += nt) {
+    const int r = q / na, b = q % na;
     if (!((mask >> r) & 1u)) continue;
     int tgt[4];
     T wa[4];
-    int n = ang_targets(W[r * na + b], nmu, nph, tgt, wa);
-    for (int k = 0; k < n; ++k) atomicAdd(&cnt[r * na + tgt[k]], 1);
+    ang_targets4(W[q], nmu, nph, tgt, wa);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (tgt[k] >= 0) atomicOr(&msk[(r * na + tgt[k]) * nwd + (b >> 5)], 1u << (b & 31));
   }
   __syncthreads();
   {
     const int warp = tid >> 5, lane = tid & 31;
-    for (int r = warp; r < nr; r += ((int)blockDim.x >> 5)) {
+    for (int r = warp; r < nr; r += (nt >> 5)) {
       if (!((mask >> r) & 1u)) continue;
-      int per = (na + 31) / 32;
-      int k0 = lane * per, k1 = min(k0 + per, na);
+      const int per = (na + 31) / 32;
+      const int k0 = min(lane * per, na), k1 = min(k0 + per, na);
       int loc = 0;
-      for (int k = k0; k < k1; ++k) loc += cnt[r * na + k];
+      for (int k = k0; k < k1; ++k)
+        for (int w = 0; w < nwd; ++w) loc += __popc(msk[(r * na + k) * nwd + w]);
       int incl = loc;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
       }
       int run = incl - loc;
       for (int k = k0; k < k1; ++k) {
-        int c = cnt[r * na + k];
         off[r * (na + 1) + k] = (short)run;
-        run += c;
-        cnt[r * na + k] = 0;
+        for (int w = 0; w < nwd; ++w) run += __popc(msk[(r * na + k) * nwd + w]);
       }
       if (lane == 31) off[r * (na + 1) + na] = (short)incl;
     }
   }
   __syncthreads();
-  for (int q = tid; q < nr * na; q += (int)blockDim.x) {
-    int r = q / na, b = q % na;
+  for (int q = tid; q < nr * na; q += nt) {
+    const int r = q / na, b = q % na;
     if (!((mask >> r) & 1u)) continue;
     int tgt[4];
     T wa[4];
-    int n = ang_targets(W[r * na + b], nmu, nph, tgt, wa);
-    for (int k = 0; k < n; ++k) {
-      int pos = off[r * (na + 1) + tgt[k]] + atomicAdd(&cnt[r * na + tgt[k]], 1);
+    ang_targets4(W[q], nmu, nph, tgt, wa);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (tgt[k] < 0) continue;
+      const unsigned* mt = msk + (r * na + tgt[k]) * nwd;
+      int pos = off[r * (na + 1) + tgt[k]];
+      for (int w = 0; w < (b >> 5); ++w) pos += __popc(mt[w]);
+      pos += __popc(mt[b >> 5] & ((1u << (b & 31)) - 1u));
       AEnt<T> e;
       e.w = wa[k];
       e.b = b;
       ent[r * 4 * na + pos] = e;
-    }
-  }
-  __syncthreads();
-  for (int q = tid; q < nr * na; q += (int)blockDim.x) {
-    int r = q / na, t = q % na;
-    if (!((mask >> r) & 1u)) continue;
-    AEnt<T>* L = ent + r * 4 * na;
-    int e0 = off[r * (na + 1) + t], e1 = off[r * (na + 1) + t + 1];
-    for (int i = e0 + 1; i < e1; ++i) {
-      AEnt<T> x = L[i];
-      int j = i - 1;
-      while (j >= e0 && L[j].b > x.b) { L[j + 1] = L[j]; --j; }
-      L[j + 1] = x;
     }
   }
   __syncthreads();
@@ -472,41 +467,52 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
 }
 
 // Angular pass for destination angle bp over the rows of this thread:
-// out(t) = sum_e w_e E[t][b_e]; the list (at most 8 entries kept in registers,
-// longer lists streamed) is read once for all rows.  The lanes of a warp run
-// the register path together up to the longest list among them (lanes with
-// shorter lists skip the extra entries), so lists of uneven length do not
-// split the warp into separate passes.
-template <typename T, typename A, typename Out>
+// out(t) = sum_e w_e E[t][b_e], the entries summed in list order.  Rows are
+// taken RB at a time and each list entry is read once for the RB rows; the
+// lanes of a warp walk the entries together up to the longest list among
+// them (a lane with a shorter list skips the rest), so lists of uneven length
+// do not split the warp into separate passes.
+template <int RB, typename T, typename A, typename Out>
+__device__ __forceinline__ void angular_block(int t0, int nch, int ne, int na, int e0, int n, int nmax,
+                                              const AEnt<T>* ent, const T* E, Out out) {
+  A acc[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) acc[j] = A(0);
+  for (int k = 0; k < nmax; ++k) {
+    if (k < n) {
+      const AEnt<T> e = ent[e0 + k];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const int t = t0 + j * nch;
+        if (t < ne) acc[j] += (A)e.w * (A)E[t * na + e.b];
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < RB; ++j) {
+    const int t = t0 + j * nch;
+    if (t < ne) out(t, acc[j]);
+  }
+}
+
+// RB = 4: rows in blocks of four.  RB = 0: blocks of four while four rows
+// remain, then of two, then single rows (no masked-off rows in a block).
+// Kernels of up to 256 threads per CTA take RB = 4 (three or more rows per
+// thread at the usual sizes; the longer code of RB = 0 made their bodies
+// slower), those of 512 take RB = 0 (two rows per thread on 80 angles and 12
+// groups, five on 128 angles and 20 groups).
+template <typename T, typename A, int RB = 4, typename Out>
 __device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int e0, int e1, const AEnt<T>* ent,
                                              const T* E, Out out) {
   const int n = e1 - e0;
   const int nmax = __reduce_max_sync(__activemask(), n);
-  if (nmax <= 8) {
-    T w[8];
-    int bb[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (k < n) { w[k] = ent[e0 + k].w; bb[k] = ent[e0 + k].b; }
-      else { w[k] = T(0); bb[k] = 0; }
-    }
-    for (int t = gc; t < ne; t += nch) {
-      const T* Er = E + t * na;
-      A acc = A(0);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (k >= nmax) break;
-        if (k < n) acc += (A)w[k] * (A)Er[bb[k]];
-      }
-      out(t, acc);
-    }
+  if (RB == 4) {
+    for (int t0 = gc; t0 < ne; t0 += 4 * nch) angular_block<4, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
   } else {
-    for (int t = gc; t < ne; t += nch) {
-      const T* Er = E + t * na;
-      A acc = A(0);
-      for (int k = e0; k < e1; ++k) acc += (A)ent[k].w * (A)Er[ent[k].b];
-      out(t, acc);
-    }
+    int t0 = gc;
+    for (; t0 + 3 * nch < ne; t0 += 4 * nch) angular_block<4, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
+    for (; t0 + nch < ne; t0 += 2 * nch) angular_block<2, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
+    for (; t0 < ne; t0 += nch) angular_block<1, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
   }
 }
 
@@ -660,7 +666,7 @@ struct FluxSmem {
   unsigned long long* bar;  // mbarrier of the stencil copies
   T* buf;          // [8][ne][nang]: 4 stencil/g buffers, 4 work buffers
   Wt<T>* W;        // [6][nang]   (aliases the work buffers)
-  int* cnt;        // [6][nang]   (aliases the work buffers)
+  unsigned* msk;   // [6][nang][ceil(nang/32)] (aliases the work buffers)
   AEnt<T>* ent;    // [6][4 nang]
   short* off;      // [6][nang + 1]
   T* n0; T* n1; T* n2;  // [nang] direction components
@@ -720,14 +726,14 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
   BT_TAKE(ridx, int, kMaxWarps);
   {
     // buf = 4 stencil buffers followed by 4 work buffers.  The remap weights
-    // and list counters live only until the lists are built, when the work
+    // and list bitmasks live only until the lists are built, when the work
     // buffers are idle; the collision scratch only after the last face.
     size_t o_b = (o + 15) & ~size_t(15);
     size_t stencil = sizeof(T) * (size_t)4 * nbin;
     size_t o_work = o_b + stencil;
     size_t o_c = (o_work + sizeof(Wt<T>) * (size_t)6 * nang + 15) & ~size_t(15);
     size_t need_work = sizeof(T) * (size_t)4 * nbin;
-    size_t need_wc = o_c + sizeof(int) * (size_t)6 * nang - o_work;
+    size_t need_wc = o_c + sizeof(unsigned) * (size_t)6 * nang * ((nang + 31) / 32) - o_work;
     size_t need_col = sizeof(double) * (size_t)2 * nw * nang;
     size_t tot = stencil + (need_work > need_wc ? need_work : need_wc);
     if (mode == 2) tot = 0;   // the zone pass stages no stencils
@@ -735,7 +741,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     if (s) {
       s->buf = reinterpret_cast<T*>(base + o_b);
       s->W = reinterpret_cast<Wt<T>*>(base + o_work);
-      s->cnt = reinterpret_cast<int*>(base + o_c);
+      s->msk = reinterpret_cast<unsigned*>(base + o_c);
       s->wr_r = reinterpret_cast<double*>(base + o_b);
       s->wr_i = reinterpret_cast<double*>(base + o_b) + (size_t)nw * nang;
     }
@@ -1053,7 +1059,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         cang[k] = ft.c6k[k] * u0 * S.dOm[gb];
       }
     }
-    build_alists(S.W, 6, mask, NA, NMU, NPH, S.off, S.cnt, S.ent);   // synchronises
+    build_alists(S.W, 6, mask, NA, NMU, NPH, S.off, S.msk, S.ent);   // synchronises
 
     for (int s = 0; s < NS; ++s) {
       // face opacities and flux-switch weights per group [R-10, R-12b]
@@ -1115,7 +1121,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           if (k == 0 && F.type != F_INTERNAL) continue;
           const short* off = S.off + slot * (NA + 1);
           StoreG<T> st_g{SRC + slot * nbin, csb, NA, gb};
-          angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
+          angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
         }
       }
       __syncthreads();
@@ -1275,11 +1281,11 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           const T* Es = side == 0 ? EP : EQ;
           const T sgn = side == 0 ? T(-1) : T(1);
           if (MODE == 0) {
-            angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es,
+            angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es,
                                AddDN<T>{S.dN + (size_t)s * nbin, NA, gb, sgn});
           } else {
             T* d = dep + (((size_t)F.z[1 + side] * 6 + 2 * F.axis + (side == 0 ? 1 : 0)) * NS + s) * nbin;
-            angular_rows<T, T>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn});
+            angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn});
           }
         }
       }
@@ -1657,7 +1663,7 @@ __global__ void __launch_bounds__(256) k_zone_collide(Tables tb, State st, doubl
 template <typename T>
 struct RemapSmem {
   T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3; T* fix;
-  Wt<T>* W; AEnt<T>* ent; short* off; int* cnt;
+  Wt<T>* W; AEnt<T>* ent; short* off; unsigned* msk;
   ff* redf; float* rkey; int* ridx;
 };
 
@@ -1684,7 +1690,7 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(W, Wt<T>, nang);
   BT_TAKE(ent, AEnt<T>, 4 * nang);
   BT_TAKE(off, short, nang + 1);
-  BT_TAKE(cnt, int, nang);
+  BT_TAKE(msk, unsigned, (size_t)nang * ((nang + 31) / 32));
   BT_TAKE(redf, ff, kWarps);
   BT_TAKE(rkey, float, kWarps);
   BT_TAKE(ridx, int, kWarps);
@@ -1693,7 +1699,7 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
+__global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RemapSmem<T> S;
   remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, &S, smem_raw);
@@ -1738,7 +1744,7 @@ __global__ void __launch_bounds__(kThreads) k_time_remap(Tables tb, State st) {
   __syncthreads();
   const int em = gact ? S.W[gb].m : 0;
   const T ew = gact ? S.W[gb].we : T(0);
-  build_alists(S.W, 1, 1u, NA, NMU, NPH, S.off, S.cnt, S.ent);
+  build_alists(S.W, 1, 1u, NA, NMU, NPH, S.off, S.msk, S.ent);
   const T c6x = (T)pow6(st.cf_old[zone]), c6y = (T)pow6(st.cf[zone]);
   T* f = reinterpret_cast<T*>(st.f);
   for (int s = 0; s < tb.n_s; ++s) {
