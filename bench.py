@@ -153,8 +153,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (207.87e6 + 1098.65e6 + 1337.83e6 + 180.50e6,
-         "97a4679c3ab4ceae8ba0bf1eefefd2ff24ea7b1225c47293b3df105237dfdd3f"),
+        (207.08e6 + 1079.48e6 + 1337.96e6 + 180.32e6,
+         "1813dcc0cedae04a08dc722f60bdb436632991c3a81a1521a8764ffe038557f7"),
 }
 
 

@@ -129,8 +129,6 @@ __device__ __forceinline__ double floor_t(double x) { return floor(x); }
 __device__ __forceinline__ float floor_t(float x) { return floorf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 __device__ __forceinline__ float log_t(float x) { return logf(x); }
-__device__ __forceinline__ double pow_t(double x, double y) { return pow(x, y); }
-__device__ __forceinline__ float pow_t(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ double atan2_t(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ float atan2_t(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double exp_t(double x) { return exp(x); }
@@ -162,8 +160,11 @@ __device__ void chain_weights_dir(const Tables& tb, const T* s_mu, const T* n, c
   T phs = atan2_t(p[2], p[1]);
   if (phs < T(0)) phs += T(2 * kPi);
   // energy: eps* = rho eps_i, bracket eps_{i+m} <= eps* < eps_{i+m+1}
-  int m = (int)floor_t(log_t(rho) / log_t(R));
-  T t = rho / pow_t(R, (T)m);
+  // (t = rho / R^m formed as exp(log rho - m log R): one exponential in
+  // place of a general power)
+  const T lrho = log_t(rho), lR = log_t(R);
+  int m = (int)floor_t(lrho / lR);
+  T t = exp_t(lrho - (T)m * lR);
   T we = (t - T(1)) / (R - T(1));
   we = we < T(0) ? T(0) : (we > T(1) ? T(1) : we);
   // mu: linear between bracketing nodes; clamped outside [mu_0, mu_last]
