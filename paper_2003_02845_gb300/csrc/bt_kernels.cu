@@ -421,11 +421,12 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
 // clamp(i+m) (weight 1-we) and clamp(i+m+1) (we), and its content per unit
 // dGamma is rescaled by dGamma_i / dGamma_t = R^(3(i-t)) (p3c[k] = R^(3k)):
 //   E[t] = c * sum_i w(t|i) R^(3(i-t)) src[i].
-// the first and last group's rows (clamped targets): a separate, not inlined
-// function keeps the hot loop of the flux kernel small (its instruction
-// fetch stalls otherwise; the same rows, the same sums)
+// the first and last group's rows (clamped targets); the flux kernel calls
+// them through energy_edge, not inlined, which keeps its hot loop small (its
+// instruction fetch stalls otherwise; the same rows, the same sums)
 template <typename T, typename A>
-__device__ __noinline__ A energy_edge(int t, int ne, int na, int b, int m, A wl, A wr, const T* src, const T* p3c) {
+__device__ __forceinline__ A energy_edge_inl(int t, int ne, int na, int b, int m, A wl, A wr, const T* src,
+                                             const T* p3c) {
   A acc = A(0);
   int lo = (t == 0) ? 0 : t - m;
   int hi = (t == ne - 1) ? ne - 1 : t - m;
@@ -438,6 +439,11 @@ __device__ __noinline__ A energy_edge(int t, int ne, int na, int b, int m, A wl,
   return acc;
 }
 
+template <typename T, typename A>
+__device__ __noinline__ A energy_edge(int t, int ne, int na, int b, int m, A wl, A wr, const T* src, const T* p3c) {
+  return energy_edge_inl<T, A>(t, ne, na, b, m, wl, wr, src, p3c);
+}
+
 template <typename T, typename A, bool kEdgeCall = false>
 __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, int b, int m, T we, const T* src, T* E,
                                               T c, const T* p3c) {
@@ -445,6 +451,28 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
   const bool small = m > -ne && m < ne;   // interior sources exist only then
   const A wli = small ? wl * (A)p3c[-m] : A(0);
   const A wri = (m >= -ne && m < ne - 1) ? wr * (A)p3c[-m - 1] : A(0);
+  if (__all_sync(__activemask(), m == 0 || m == -1)) {
+    // shifts of less than one group (the usual case): both taps of every
+    // interior row lie in range, so the rows need no bounds checks; the
+    // edge rows as below.  Same operations in the same order.
+    int t = gc;
+    if (t == 0) {
+      E[b] = (T)(kEdgeCall ? energy_edge<T, A>(0, ne, na, b, m, wl, wr, src, p3c)
+                           : energy_edge_inl<T, A>(0, ne, na, b, m, wl, wr, src, p3c));
+      t += nch;
+    }
+    const T* sL = src + (t - m) * na + b;   // tap t - m; the other tap is one row lower
+    for (; t < ne - 1; t += nch, sL += nch * na) {
+      A acc = A(0);
+      acc += wli * (A)sL[0];
+      acc += wri * (A)sL[-na];
+      E[t * na + b] = (T)acc;
+    }
+    if (t == ne - 1)
+      E[t * na + b] = (T)(kEdgeCall ? energy_edge<T, A>(t, ne, na, b, m, wl, wr, src, p3c)
+                                    : energy_edge_inl<T, A>(t, ne, na, b, m, wl, wr, src, p3c));
+    return;
+  }
   for (int t = gc; t < ne; t += nch) {
     A acc = A(0);
     if (t > 0 && t < ne - 1) {
@@ -454,14 +482,7 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
     } else if (kEdgeCall) {
       acc = energy_edge<T, A>(t, ne, na, b, m, wl, wr, src, p3c);
     } else {
-      int lo = (t == 0) ? 0 : t - m;
-      int hi = (t == ne - 1) ? ne - 1 : t - m;
-      lo = max(lo, 0); hi = min(hi, ne - 1);
-      for (int i = lo; i <= hi; ++i) acc += wl * (A)p3c[i - t] * (A)src[i * na + b];
-      lo = (t == 0) ? 0 : t - m - 1;
-      hi = (t == ne - 1) ? ne - 1 : t - m - 1;
-      lo = max(lo, 0); hi = min(hi, ne - 1);
-      for (int i = lo; i <= hi; ++i) acc += wr * (A)p3c[i - t] * (A)src[i * na + b];
+      acc = energy_edge_inl<T, A>(t, ne, na, b, m, wl, wr, src, p3c);
     }
     E[t * na + b] = (T)acc;
   }
