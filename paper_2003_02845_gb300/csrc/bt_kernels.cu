@@ -54,6 +54,7 @@ struct Loc {
   T v[3];
   T g, gg;   // gamma and gamma^2/(gamma+1)
   T al, cf;
+  T ral, rcf;   // 1/alpha, 1/phi (formed once per location)
 };
 
 template <typename T>
@@ -63,6 +64,7 @@ __device__ __forceinline__ void make_loc(Loc<T>& L, const double* v, double al, 
   L.g = T(1) / sqrt(T(1) - v2);
   L.gg = L.g * L.g / (L.g + T(1));
   L.al = (T)al; L.cf = (T)cf;
+  L.ral = T(1) / L.al; L.rcf = T(1) / L.cf;
 }
 
 template <typename T>
@@ -134,16 +136,32 @@ __device__ __forceinline__ float atan2_t(float y, float x) { return atan2f(y, x)
 __device__ __forceinline__ double exp_t(double x) { return exp(x); }
 __device__ __forceinline__ float exp_t(float x) { return expf(x); }
 
+// constants of the energy bracket on a grid of ratio R, formed once per
+// thread: log R, 1/log R, 1/(R-1)
+template <typename T>
+struct EBr {
+  T lR, rlR, rRm1;
+};
+template <typename T>
+__device__ __forceinline__ EBr<T> make_ebr(T R) {
+  EBr<T> k;
+  k.lR = log_t(R);
+  k.rlR = T(1) / k.lR;
+  k.rRm1 = T(1) / (R - T(1));
+  return k;
+}
+
 // Full chain for source angle `ang`: comoving(src) -> Eulerian(src) -> kick
 // -> rotation G (src triad -> dst triad; transposed if gT) -> comoving(dst),
 // then the trilinear weights (Sec. 3.2, Eq. interpolation).
 template <typename T>
 __device__ void chain_weights_dir(const Tables& tb, const T* s_mu, const T* n, const Loc<T>& X, const Loc<T>& Y,
-                                  const T* G, int gT, int axis, T R, Wt<T>& w) {
+                                  const T* G, int gT, int axis, const EBr<T>& K, Wt<T>& w) {
   T e, p[3];
   boost_fwd(X, n, e, p);
-  T a = X.al / Y.al;
-  T bq = (X.cf / Y.cf) * (X.cf / Y.cf);
+  const T a = X.al * Y.ral;
+  const T cr = X.cf * Y.rcf;
+  const T bq = cr * cr;
   kick(axis, a, bq, e, p);
   if (G) {
     T q[3];
@@ -162,10 +180,10 @@ __device__ void chain_weights_dir(const Tables& tb, const T* s_mu, const T* n, c
   // energy: eps* = rho eps_i, bracket eps_{i+m} <= eps* < eps_{i+m+1}
   // (t = rho / R^m formed as exp(log rho - m log R): one exponential in
   // place of a general power)
-  const T lrho = log_t(rho), lR = log_t(R);
-  int m = (int)floor_t(lrho / lR);
-  T t = exp_t(lrho - (T)m * lR);
-  T we = (t - T(1)) / (R - T(1));
+  const T lrho = log_t(rho);
+  int m = (int)floor_t(lrho * K.rlR);
+  T t = exp_t(lrho - (T)m * K.lR);
+  T we = (t - T(1)) * K.rRm1;
   we = we < T(0) ? T(0) : (we > T(1) ? T(1) : we);
   // mu: linear between bracketing nodes; clamped outside [mu_0, mu_last]
   int jL;
@@ -176,6 +194,8 @@ __device__ void chain_weights_dir(const Tables& tb, const T* s_mu, const T* n, c
   } else if (mus >= s_mu[nmu - 1]) {
     jL = nmu - 2; wm = T(1);
   } else {
+    // the last node at or below mu* (a linear walk: measured faster than a
+    // bisection on 8 nodes)
     jL = 0;
     while (jL < nmu - 2 && s_mu[jL + 1] <= mus) ++jL;
     wm = (mus - s_mu[jL]) / (s_mu[jL + 1] - s_mu[jL]);
@@ -200,9 +220,9 @@ __device__ void chain_weights_dir(const Tables& tb, const T* s_mu, const T* n, c
 template <typename T>
 __device__ __forceinline__ void chain_weights(const Tables& tb, const T* s_mu, const T* n0, const T* n1, const T* n2,
                                               const Loc<T>& X, const Loc<T>& Y, const T* G, int gT, int axis, int ang,
-                                              T R, Wt<T>& w) {
+                                              const EBr<T>& K, Wt<T>& w) {
   const T n[3] = {n0[ang], n1[ang], n2[ang]};
-  chain_weights_dir(tb, s_mu, n, X, Y, G, gT, axis, R, w);
+  chain_weights_dir(tb, s_mu, n, X, Y, G, gT, axis, K, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -1029,7 +1049,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     // --- weights of the six remaps: slots 0..3 -> face, face -> slot 1, face -> slot 2
     const Loc<T>* LF = S.L + 5 * fidx;
     const T* GF = S.Gs + 36 * fidx;
-    const T Rg = (T)tb.R;
+    const EBr<T> Rg = make_ebr<T>((T)tb.R);
     {
       const Loc<T> Ls = LF[4];
       for (int q = tid; q < 6 * NA; q += NT) {
@@ -1756,7 +1776,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st)
   Loc<T> X, Y;
   make_loc(X, st.v_old + 3 * zone, st.al_old[zone], st.cf_old[zone]);
   make_loc(Y, st.v + 3 * zone, st.al[zone], st.cf[zone]);
-  const T Rg = (T)tb.R;
+  const EBr<T> Rg = make_ebr<T>((T)tb.R);
   for (int ang = tid; ang < NA; ang += kThreads) {
     if (sizeof(T) == 4 && st.sur_tab)
       S.W[ang] = reinterpret_cast<const Wt<T>*>(st.sur_tab)[(size_t)zone * kSurKindsAll * NA + ang];
@@ -2094,7 +2114,7 @@ __global__ void k_sur_samples(Tables tb, State st, const int* idx, long long n, 
       make_loc(LY, R.vY, R.alY, R.cfY);
       const double n3[3] = {f[0], f[1], f[2]};
       Wt<double> w;
-      chain_weights_dir<double>(tb, tb.mu, n3, LX, LY, R.G, R.gT, R.axis, tb.R, w);
+      chain_weights_dir<double>(tb, tb.mu, n3, LX, LY, R.G, R.gT, R.axis, make_ebr<double>(tb.R), w);
       v = sur_targets(tb, w, ang, y) ? 1 : 2;
     }
     for (int q = 0; q < 16; ++q) X[16 * i + q] = (float)f[q];
@@ -2175,7 +2195,7 @@ __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const 
   unsigned phase = 0;
   bool ok = true;
   unsigned long long n_eval = 0, n_trip = 0;
-  const float Rf = (float)tb.R;
+  const EBr<float> Rf = make_ebr<float>((float)tb.R);
   for (int zone = blockIdx.x; zone < tb.n_zone && ok; zone += gridDim.x) {
     if (t < kSurKindsAll) {
       SurXfer& x = xf[t];
