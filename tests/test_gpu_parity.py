@@ -105,6 +105,28 @@ def test_fp64_single_group_single_phi(orc, gpu):
     compare_run(orc, gpu, p, 5)
 
 
+def narrow_groups(p, ratio=1.06):
+    """Regrid p's energy groups to a ratio close to 1: the Doppler and lapse
+    shifts of the moving backgrounds then move content by several groups
+    (about one row in nine of the remaps cannot be written with offsets of
+    one), so the energy pass's general rows and its clamped edge rows with
+    several terms run, not only the sub-group shifts."""
+    ne = len(p.eps_edges) - 1
+    p.eps_edges = np.geomspace(1.0, ratio ** ne, ne + 1)
+    return p
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
+def test_shifts_of_several_groups(orc, gpu, precision, tol):
+    p = narrow_groups(W.random_column(14, n_r=10, n_e=8, n_mu=6, n_phi=4, n_s=2))
+    compare_run(orc, gpu, p, 10, precision=precision, tol=tol)
+
+
+def test_fp64_2d_shifts_of_several_groups(orc, gpu):
+    p = narrow_groups(W.random_2d(15, n_r=7, n_theta=4, n_e=6, n_mu=4, n_phi=6, n_s=1))
+    compare_run(orc, gpu, p, 6)
+
+
 # ---------------------------------------------------------------------------
 # Mixed precision path
 # ---------------------------------------------------------------------------

@@ -27,12 +27,16 @@ def _cases():
     sphere.f0 = np.random.default_rng(3).uniform(0, 1, sphere.f0.shape)
     slab = W.slab_diffusion(kappa_s=30.0, dz=0.02, z_max=0.3, n_mu=6)
     slab.f0 = slab.f0 * np.random.default_rng(8).uniform(0.5, 1.5, slab.f0.shape)
+    narrow = W.random_2d(15, n_r=7, n_theta=4, n_e=6, n_mu=4, n_phi=6, n_s=2)
+    narrow.eps_edges = np.geomspace(1.0, 1.06 ** 6, 7)
     return {
         "column": W.random_column(1, n_r=11, n_e=5, n_mu=6, n_phi=4, n_s=2),
         "origin": sphere,
         "2d": W.random_2d(4, n_r=9, n_theta=5, n_e=4, n_mu=4, n_phi=6, n_s=2),
         "2d_origin_ragged": W.random_2d(6, n_r=7, n_theta=3, n_e=3, n_mu=5, n_phi=7, n_s=1, r_min=0.0),
         "slab": slab,
+        # shifts of several energy groups (the energy pass's general rows)
+        "2d_narrow_groups": narrow,
     }
 
 
@@ -50,7 +54,7 @@ def _run(gpu, p, precision, shape, steps, dt):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", ["column", "origin", "2d", "2d_origin_ragged", "slab"])
+@pytest.mark.parametrize("case", ["column", "origin", "2d", "2d_origin_ragged", "slab", "2d_narrow_groups"])
 def test_split_equals_fused(gpu, case, precision):
     p = _cases()[case]
     a = _run(gpu, p, precision, 256, 6, 0.004)
