@@ -1704,7 +1704,7 @@ __global__ void __launch_bounds__(256) k_zone_collide(Tables tb, State st, doubl
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RemapSmem {
-  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3; T* fix;
+  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3;
   Wt<T>* W; AEnt<T>* ent; short* off; unsigned* msk;
   ff* redf; float* rkey; int* ridx;
 };
@@ -1721,7 +1721,6 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(src, T, (size_t)ne * nang);
   BT_TAKE(E, T, (size_t)ne * nang);
   BT_TAKE(dst, T, (size_t)ne * nang);
-  BT_TAKE(fix, T, 1);
   BT_TAKE(mu, T, nmu);
   BT_TAKE(n0, T, nang);
   BT_TAKE(n1, T, nang);
@@ -1733,9 +1732,9 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(ent, AEnt<T>, 4 * nang);
   BT_TAKE(off, short, nang + 1);
   BT_TAKE(msk, unsigned, (size_t)nang * ((nang + 31) / 32));
-  BT_TAKE(redf, ff, kWarps);
-  BT_TAKE(rkey, float, kWarps);
-  BT_TAKE(ridx, int, kWarps);
+  BT_TAKE(redf, ff, 4 * kWarps);     // [species parity][input, output total][warp]
+  BT_TAKE(rkey, float, 2 * kWarps);  // [species parity][warp]
+  BT_TAKE(ridx, int, 2 * kWarps);
 #undef BT_TAKE
   return (o + 15) & ~size_t(15);
 }
@@ -1789,8 +1788,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st)
   build_alists(S.W, 1, 1u, NA, NMU, NPH, S.off, S.msk, S.ent);
   const T c6x = (T)pow6(st.cf_old[zone]), c6y = (T)pow6(st.cf[zone]);
   T* f = reinterpret_cast<T*>(st.f);
+  const int lane = tid & 31, warp = tid >> 5;
+  // Per species three block barriers (two in FP64): the energy pass reads its
+  // column's rows of other threads, the angular pass other columns; every
+  // thread's angular rows are its own bins, so the correction's partials
+  // need no barrier before them, and every thread combines the warps'
+  // partials itself (no barrier after).  The partials alternate between two
+  // buffers by species parity: a thread that starts the next species cannot
+  // overwrite what a slower one still combines.
   for (int s = 0; s < tb.n_s; ++s) {
     T* fz = f + ((size_t)s * tb.n_zone + zone) * nbin;
+    ff* pin = S.redf + (s & 1) * 2 * kWarps;      // [0, kWarps): input total, then output total
+    float* pk = S.rkey + (s & 1) * kWarps;
+    int* pi = S.ridx + (s & 1) * kWarps;
     // content per unit dGamma of the old frame: y = phi^6 u0 dOmega f
     ff part = ff{0.0f, 0.0f};
     if (gact) {
@@ -1803,45 +1813,68 @@ __global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st)
         if (sizeof(T) == 4) part = ff_add(part, two_prod((float)d, (float)S.dGam[i]));
       }
     }
-    ff tot_in = ff{0.0f, 0.0f};
-    if (sizeof(T) == 4) tot_in = block_sum_ff(part, S.redf);
-    else __syncthreads();
+    if (sizeof(T) == 4) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part = ff_add(part, ff_shfl_down(part, o));
+      if (lane == 0) pin[warp] = part;
+    }
+    __syncthreads();
     if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, S.src, S.E, T(1), P3);
     __syncthreads();
-    if (gact) angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
-    __syncthreads();
+    // the remapped rows (this thread's own bins), with the mixed path's
+    // partials of the exact-total correction: total and largest bin
+    ff partc = ff{0.0f, 0.0f};
+    float bk = -1.0f;
+    int bi = 0x7fffffff;
+    if (gact) {
+      angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
+      if (sizeof(T) == 4)
+        for (int i = gc; i < NE; i += nch) {
+          const int q = i * NA + gb;
+          partc = ff_add(partc, two_prod((float)S.dst[q], (float)S.dGam[i]));
+          const float k = fabsf((float)S.dst[q] * (float)S.dGam[i]);
+          if (k > bk) { bk = k; bi = q; }
+        }
+    }
     int at = -1;
-    double corr_y = 0.0;
+    ff tot_in = ff{0.0f, 0.0f}, tot = ff{0.0f, 0.0f};
     if (sizeof(T) == 4) {
       // restore the exact content total of the zone (float gathers round)
-      ff partc = ff{0.0f, 0.0f};
-      float bk = -1.0f;
-      int bi = 0x7fffffff;
-      for (int q = tid; q < nbin; q += kThreads) {
-        partc = ff_add(partc, two_prod((float)S.dst[q], (float)S.dGam[q / NA]));
-        float k = fabsf((float)S.dst[q] * (float)S.dGam[q / NA]);
-        if (k > bk) { bk = k; bi = q; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        partc = ff_add(partc, ff_shfl_down(partc, o));
+        const float k2 = __shfl_down_sync(0xffffffffu, bk, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+        if (k2 > bk || (k2 == bk && i2 < bi)) { bk = k2; bi = i2; }
       }
-      ff tot = block_sum_ff(partc, S.redf);
-      at = block_argmax(bk, bi, S.rkey, S.ridx);
-      // the corrected value of bin `at`, formed once (float64 work by every
-      // thread, or per bin, would run on GB300's narrow float64 pipe)
-      if (tid == 0) {
-        corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
-        S.fix[0] = (T)((double)S.dst[at] + corr_y);
-      }
+      if (lane == 0) { pin[kWarps + warp] = partc; pk[warp] = bk; pi[warp] = bi; }
       __syncthreads();
+      tot_in = pin[0];
+      tot = pin[kWarps];
+      float kb = pk[0];
+      at = pi[0];
+      for (int w = 1; w < kWarps; ++w) {
+        tot_in = ff_add(tot_in, pin[w]);
+        tot = ff_add(tot, pin[kWarps + w]);
+        if (pk[w] > kb || (pk[w] == kb && pi[w] < at)) { kb = pk[w]; at = pi[w]; }
+      }
     }
     if (gact) {
       const T u0 = Y.g * (T(1) + (Y.v[0] * S.n0[gb] + Y.v[1] * S.n1[gb] + Y.v[2] * S.n2[gb]));
       const T cang = c6y * u0 * S.dOm[gb];
       for (int ip = gc; ip < NE; ip += nch) {
         const int q = ip * NA + gb;
-        const T d = q == at ? S.fix[0] : S.dst[q];
+        T d = S.dst[q];
+        if (q == at) {
+          // the corrected value of bin `at`, formed once by its owner
+          // (float64 work by every thread, or per bin, would run on GB300's
+          // narrow float64 pipe)
+          const double corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
+          d = (T)((double)d + corr_y);
+        }
         fz[q] = d / cang;
       }
     }
-    __syncthreads();
   }
 }
 
