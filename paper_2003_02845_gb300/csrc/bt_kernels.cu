@@ -928,6 +928,39 @@ __device__ __forceinline__ bool face_exists(const Tables& tb, int a, int b, int 
   return tb.area_p[b * nr + a] != 0.0;
 }
 
+// The zone pass's exact deposit totals and outflow tallies from the face
+// pass's records: lane s of the calling warp sums species s's records (faces
+// in order, Q side then P side) in registers, the species in parallel.  Not
+// inlined: inlined into the zone pass it raised that kernel's registers from
+// 48 to 92.
+__device__ __noinline__ void zone_records(const Tables& tb, const DepRec* rec, int zone, int a, int b, int nface,
+                                          int NS, bool mixed, ff* dtot, double* tally) {
+  const int lane = threadIdx.x & 31;
+  for (int s = lane; s < NS; s += 32) {
+    ff dt = dtot[s];
+    double t0 = tally[2 * s], t1 = tally[2 * s + 1];
+    for (int fidx = 0; fidx < nface; ++fidx) {
+      if (!face_exists(tb, a, b, fidx)) continue;
+      const int axis = fidx < 2 ? 0 : (fidx < 4 ? 1 : 2);
+      const bool isP = fidx == 1 || fidx == 3 || fidx == 4 || (fidx == 2 && tb.periodic_th);
+      const bool isQ = fidx == 0 || fidx == 4 || (fidx == 2);
+      const DepRec* rP = isP ? rec + ((size_t)zone * 6 + 2 * axis + 1) * NS + s : nullptr;
+      const DepRec* rQ = isQ ? rec + ((size_t)zone * 6 + 2 * axis) * NS + s : nullptr;
+      if (mixed) {
+        if (rQ) dt = ff_add(dt, rQ->sum);
+        if (rP) dt = ff_add(dt, rP->sum);
+      }
+      // an outflow face has one side; the other side's record holds 0
+      const double tn = (rP ? rP->tn : 0.0) + (rQ ? rQ->tn : 0.0);
+      const double te = (rP ? rP->te : 0.0) + (rQ ? rQ->te : 0.0);
+      if (tn != 0.0 || te != 0.0) { t0 += tn; t1 += te; }
+    }
+    dtot[s] = dt;
+    tally[2 * s] = t0;
+    tally[2 * s + 1] = t1;
+  }
+}
+
 template <typename T>
 struct AddDN {   // dN += sign * T[F]
   typename DNT<T>::type* dn; int na, b; T sign;
@@ -1350,27 +1383,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       if (isQ) rows[nrow++] = 2 * axis;
     }
     // exact totals and outflow tallies of the zone's records
-    for (int fidx = 0; fidx < nface; ++fidx) {
-      if (!face_exists(tb, a, b, fidx)) continue;
-      const int axis = fidx < 2 ? 0 : (fidx < 4 ? 1 : 2);
-      const bool isP = fidx == 1 || fidx == 3 || fidx == 4 || (fidx == 2 && tb.periodic_th);
-      const bool isQ = fidx == 0 || fidx == 4 || (fidx == 2);
-      const int slotP = 2 * axis + 1, slotQ = 2 * axis;
-      for (int s = 0; s < NS; ++s) {
-        if (tid == 0) {
-          const DepRec* rP = isP ? rec + ((size_t)zone * 6 + slotP) * NS + s : nullptr;
-          const DepRec* rQ = isQ ? rec + ((size_t)zone * 6 + slotQ) * NS + s : nullptr;
-          if (sizeof(T) == 4) {
-            if (rQ) S.dtot[s] = ff_add(S.dtot[s], rQ->sum);
-            if (rP) S.dtot[s] = ff_add(S.dtot[s], rP->sum);
-          }
-          // an outflow face has one side; the other side's record holds 0
-          const double tn = (rP ? rP->tn : 0.0) + (rQ ? rQ->tn : 0.0);
-          const double te = (rP ? rP->te : 0.0) + (rQ ? rQ->te : 0.0);
-          if (tn != 0.0 || te != 0.0) { S.tally[2 * s] += tn; S.tally[2 * s + 1] += te; }
-        }
-      }
-    }
+    if (warp == 0) zone_records(tb, rec, zone, a, b, nface, NS, sizeof(T) == 4, S.dtot, S.tally);
     for (int s = 0; s < NS; ++s) {
       // all of an element's rows are loaded before they are summed in order;
       // the mixed path's exact-total correction is found in the same pass
@@ -1695,7 +1708,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 1024 / N
   flux_body<T, NT, 1>(tb, st, dt, dep, rec);
 }
 template <typename T>
-__global__ void __launch_bounds__(256) k_zone_collide(Tables tb, State st, double dt, T* dep, DepRec* rec) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_zone_collide(Tables tb, State st, double dt, T* dep, DepRec* rec) {
   flux_body<T, 256, 2>(tb, st, dt, dep, rec);
 }
 
