@@ -805,11 +805,11 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
   BT_TAKE(taus, T, nang);
   BT_TAKE(vdx, T, nang);
   BT_TAKE(rowJ, T, ne);
-  BT_TAKE(kaS, T, ne);
-  BT_TAKE(ksS, T, ne);
-  BT_TAKE(feS, T, ne);
-  BT_TAKE(wP, T, ne);
-  BT_TAKE(wQ, T, ne);
+  BT_TAKE(kaS, T, mode == 2 ? 0 : (size_t)ns * ne);
+  BT_TAKE(ksS, T, mode == 2 ? 0 : (size_t)ns * ne);
+  BT_TAKE(feS, T, mode == 2 ? 0 : (size_t)ns * ne);
+  BT_TAKE(wP, T, mode == 2 ? 0 : (size_t)ns * ne);
+  BT_TAKE(wQ, T, mode == 2 ? 0 : (size_t)ns * ne);
   BT_TAKE(F, FaceDesc, kFaces);
   BT_TAKE(FT, FaceT<T>, kFaces);
   BT_TAKE(L, Loc<T>, kFaces * 5);
@@ -1102,6 +1102,22 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         }
         S.W[r * NA + ang] = w;
       }
+      // face opacities and flux-switch weights per species and group
+      // [R-10, R-12b], all species at once: their loads overlap the weights'
+      // arithmetic instead of stalling each species' start
+      if (F.type == F_INTERNAL) {
+        for (int q = tid; q < NS * NE; q += NT) {
+          const int sq = q / NE, i = q % NE;
+          size_t oP = ((size_t)sq * tb.n_zone + F.z[1]) * NE + i;
+          size_t oQ = ((size_t)sq * tb.n_zone + F.z[2]) * NE + i;
+          double kaP = st.ka[oP], kaQ = st.ka[oQ], ksP = st.ks[oP], ksQ = st.ks[oQ];
+          S.kaS[q] = (T)(0.5 * (kaP + kaQ));
+          S.ksS[q] = (T)(0.5 * (ksP + ksQ));
+          S.feS[q] = (T)(0.5 * (st.fe[oP] + st.fe[oQ]));
+          S.wP[q] = exp_t((T)(-(kaP + ksP)) * ft.dx);
+          S.wQ[q] = exp_t((T)(-(kaQ + ksQ)) * ft.dx);
+        }
+      }
       // face bins: Eulerian energy factor and normal coordinate velocity
       for (int ang = tid; ang < NA; ang += NT) {
         T n[3] = {S.n0[ang], S.n1[ang], S.n2[ang]};
@@ -1137,19 +1153,12 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     build_alists(S.W, 6, mask, NA, NMU, NPH, S.off, S.msk, S.ent);   // synchronises
 
     for (int s = 0; s < NS; ++s) {
-      // face opacities and flux-switch weights per group [R-10, R-12b]
-      if (F.type == F_INTERNAL) {
-        for (int i = tid; i < NE; i += NT) {
-          size_t oP = ((size_t)s * tb.n_zone + F.z[1]) * NE + i;
-          size_t oQ = ((size_t)s * tb.n_zone + F.z[2]) * NE + i;
-          double kaP = st.ka[oP], kaQ = st.ka[oQ], ksP = st.ks[oP], ksQ = st.ks[oQ];
-          S.kaS[i] = (T)(0.5 * (kaP + kaQ));
-          S.ksS[i] = (T)(0.5 * (ksP + ksQ));
-          S.feS[i] = (T)(0.5 * (st.fe[oP] + st.fe[oQ]));
-          S.wP[i] = exp_t((T)(-(kaP + ksP)) * ft.dx);
-          S.wQ[i] = exp_t((T)(-(kaQ + ksQ)) * ft.dx);
-        }
-      }
+      // this species' face opacities and flux-switch weights
+      const T* kaS = S.kaS + (size_t)s * NE;
+      const T* ksS = S.ksS + (size_t)s * NE;
+      const T* feS = S.feS + (size_t)s * NE;
+      const T* wPs = S.wP + (size_t)s * NE;
+      const T* wQs = S.wQ + (size_t)s * NE;
       // stencil rows of this species (f as stored)
       if (use_tma) {
         bool ok = mbar_wait(S.bar, tphase, st.flag);
@@ -1215,8 +1224,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           for (int i = gc; i < NE; i += nch) {
             const int q = i * NA + gb;
             const T g1 = G1[q], g2 = G2[q];
-            const T r = T(0.5) * (g1 + g2) - vdx * (g2 - g1) + tau * S.kaS[i] * S.feS[i];
-            const T iD = T(1) / (T(1) + (S.kaS[i] + S.ksS[i]) * tau);
+            const T r = T(0.5) * (g1 + g2) - vdx * (g2 - g1) + tau * kaS[i] * feS[i];
+            const T iD = T(1) / (T(1) + (kaS[i] + ksS[i]) * tau);
             RD[q] = r * iD;
             ID[q] = iD;
           }
@@ -1225,7 +1234,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         // J per group (Sherman-Morrison closed form; one warp per row)
         for (int i = warp; i < NE; i += (NT / 32)) {
           T sr = T(0), s1 = T(0);
-          const T ka = S.kaS[i];
+          const T ka = kaS[i];
           for (int ang = lane; ang < NA; ang += 32) {
             const int q = i * NA + ang;
             const T dom = S.dOm[ang];
@@ -1257,18 +1266,18 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           T fs;
           if (F.type == F_INTERNAL) {
             const T g1 = G1[q], g2 = G2[q];
-            const T flw = RD[q] + S.ksS[i] * S.rowJ[i] * taug * ID[q];
+            const T flw = RD[q] + ksS[i] * S.rowJ[i] * taug * ID[q];
             T fu, w;
             if (up) {
               T sl = T(0);
               if (F.z[0] >= 0) sl = mc_limiter((g1 - G0[q]) * ft.rdl0, (g2 - g1) * ft.rdl1);
               fu = g1 + sl * ft.sP;
-              w = S.wP[i];
+              w = wPs[i];
             } else {
               T sl = T(0);
               if (F.z[3] >= 0) sl = mc_limiter((g2 - g1) * ft.rdl1, (G3[q] - g2) * ft.rdl2);
               fu = g2 + sl * ft.sQ;
-              w = S.wQ[i];
+              w = wQs[i];
             }
             fs = (T(1) - w) * flw + w * fu;
           } else if (F.type == F_OUTFLOW_P) {
