@@ -153,8 +153,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (207.08e6 + 1079.48e6 + 1337.96e6 + 180.32e6,
-         "1813dcc0cedae04a08dc722f60bdb436632991c3a81a1521a8764ffe038557f7"),
+        (208.29e6 + 1079.68e6 + 1343.23e6 + 213.08e6,
+         "0a1494c7b702e900dded46501f743c8d4d436fded5dbf1392d19dcd62784677d"),
 }
 
 
