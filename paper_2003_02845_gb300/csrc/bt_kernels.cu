@@ -1181,12 +1181,18 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         __syncthreads();
       }
       // energy pass of the stencil remaps (content density folded in)
+      // (float32: one copy of the pass for the four cells, not four, so the
+      // kernel body stays smaller and its instruction fetch stalls less;
+      // float64, whose float64 pipe is the bound, keeps the four copies)
       if (gact) {
-#pragma unroll
+#pragma unroll (sizeof(T) == 4 ? 1 : 4)
         for (int slot = 0; slot < 4; ++slot)
-          if (F.z[slot] >= 0 && (F.type == F_INTERNAL || slot == 1 || slot == 2))
-            energy_column<T, T, true>(gc, nch, NE, NA, gb, em[slot], ew[slot], SRC + slot * nbin, EB + slot * nbin,
-                                cang[slot], P3);
+          if (F.z[slot] >= 0 && (F.type == F_INTERNAL || slot == 1 || slot == 2)) {
+            const int m = slot == 0 ? em[0] : slot == 1 ? em[1] : slot == 2 ? em[2] : em[3];
+            const T we = slot == 0 ? ew[0] : slot == 1 ? ew[1] : slot == 2 ? ew[2] : ew[3];
+            const T c = slot == 0 ? cang[0] : slot == 1 ? cang[1] : slot == 2 ? cang[2] : cang[3];
+            energy_column<T, T, true>(gc, nch, NE, NA, gb, m, we, SRC + slot * nbin, EB + slot * nbin, c, P3);
+          }
       }
       __syncthreads();
       // angular pass: g_k = T_{k->s}[n_k] as face distribution (into SRC)
