@@ -153,8 +153,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (208.29e6 + 1079.68e6 + 1343.23e6 + 213.08e6,
-         "0a1494c7b702e900dded46501f743c8d4d436fded5dbf1392d19dcd62784677d"),
+        (207.70e6 + 1080.02e6 + 1343.84e6 + 212.98e6,
+         "aa498b3f4abc73091d3f131afbffdb0475978a8a2cfad76a1d160da5689358dc"),
 }
 
 
