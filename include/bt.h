@@ -244,7 +244,7 @@ int bt_weighted_totals_noalloc(const void* f, int precision, int n_s, int n_zone
 /* ------------------------------------------------------------------------
  * Learned remap: a small network that predicts the remap's redistribution
  * weights (the paper has no counterpart; its remap weights are the exact
- * trilinear ones of Sec. 3.2, which stay the judge and the fallback).
+ * trilinear ones of Sec. 3.2, which stay the check and the fallback).
  *
  * Network: x (BT_SUR_NIN = 16 features) -> normalise (x - mean) * scale ->
  * 64 -> 64 -> 64 (GELU, exact erf form) -> 27 logits -> softmax P over the

@@ -103,7 +103,7 @@ int launch_jhk(const Tables& T, const State& S, int mixed, double* J, double* H,
 int launch_check_finite(const Tables& T, const State& S, int mixed, void* stream);
 // learned remap: features X [n][16], exact targets Y [n][27] and validity of
 // the rows idx [n][3] = (zone, kind, source angle)
-// learned remap: fill st.sur_tab with the network's weights (judged against
+// learned remap: fill st.sur_tab with the network's weights (checked against
 // the exact ones; tripped rows take the exact weights) for the rows the step
 // reads (split != 0: the split flux form, which reads only owned faces).
 // counts [2]: rows evaluated, rows tripped (uint64, accumulated).

@@ -2189,7 +2189,7 @@ __global__ void k_sur_samples(Tables tb, State st, const int* idx, long long n, 
 // evaluates the network on the zone's 31 x n_ang remap rows (tensor cores,
 // 128-row tiles), projects each predicted distribution onto the trilinear
 // family by its mean offset per axis (exact when the prediction equals the
-// exact weights, which are trilinear), and judges it against the exact
+// exact weights, which are trilinear), and checks it against the exact
 // float32 weights of the same row: a row whose mean offsets differ by tol or
 // more on any axis trips and takes the exact weights.  Both weight forms sum
 // to one per axis, so number is conserved either way.
@@ -2307,7 +2307,7 @@ __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const 
       if (!ok || !valid) continue;
       tc::softmax27(z, p);
       const SurXfer& X = xf[kind];
-      // exact weights of the row (the judge and the fallback)
+      // exact weights of the row (the check and the fallback)
       Wt<float> ex;
       const float nd[3] = {n0[ang], n1[ang], n2[ang]};
       chain_weights_dir<float>(tb, smu, nd, X.X, X.Y, X.hasG ? X.G : nullptr, X.gT, X.axis, Rf, ex);
