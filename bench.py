@@ -154,7 +154,7 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
         (207.70e6 + 1080.02e6 + 1343.84e6 + 212.98e6,
-         "aa498b3f4abc73091d3f131afbffdb0475978a8a2cfad76a1d160da5689358dc"),
+         "b32066d1b79a5d896d1a8a8a1637850922d3842c3fb8d79420ed0027e65882ed"),
 }
 
 
