@@ -147,25 +147,35 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one flux
 # launch from an ncu capture of this bench's small invocation, keyed by
-# workload, precision and launch shape, and valid only for the kernel source
-# it was taken on: a changed bt_kernels.cu reports null until re-captured.
+# workload, precision and launch shape, and valid only for the kernel code
+# it was taken on (a fingerprint of bt_kernels.cu without its comments and
+# blank lines): changed kernel code reports null until re-captured.
 # For the split form the figure is the face pass plus the zone pass: f read
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
         (207.70e6 + 1080.02e6 + 1343.84e6 + 212.98e6,
-         "b32066d1b79a5d896d1a8a8a1637850922d3842c3fb8d79420ed0027e65882ed"),
+         "3b005c99538126eae2efd4b6208a92118038e331e43108b1f74575dcb57f8dc2"),
 }
 
 
-def measured_traffic(workload, precision, nt):
+def kernel_fingerprint(path=None):
+    """sha256 of the kernel source with comments, blank lines and trailing
+    spaces removed (a comment-only edit keeps it)."""
     import hashlib
+    import re
+    path = path or os.path.join(ROOT, "paper_2003_02845_gb300", "csrc", "bt_kernels.cu")
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
+
+
+def measured_traffic(workload, precision, nt):
     rec = TRAFFIC.get((workload, precision, nt))
     if rec is None:
         return None
-    src = os.path.join(ROOT, "paper_2003_02845_gb300", "csrc", "bt_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return rec[0] if sha == rec[1] else None
+    return rec[0] if kernel_fingerprint() == rec[1] else None
 
 
 def algorithmic_flops_per_bin(prob):
