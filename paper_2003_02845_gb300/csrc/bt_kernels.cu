@@ -1237,22 +1237,48 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           }
         }
         __syncthreads();
-        // J per group (Sherman-Morrison closed form; one warp per row)
-        for (int i = warp; i < NE; i += (NT / 32)) {
-          T sr = T(0), s1 = T(0);
-          const T ka = kaS[i];
-          for (int ang = lane; ang < NA; ang += 32) {
-            const int q = i * NA + ang;
-            const T dom = S.dOm[ang];
-            sr += dom * RD[q];
-            s1 += dom * ID[q] * (T(1) + ka * S.taus[ang]);
-          }
+        // J per group (Sherman-Morrison closed form).  float32: one half-warp
+        // per row (12 rows fill 256 threads in one round, every lane busy on
+        // 80 angles); float64: one warp per row.  Either way the order of the
+        // row sums does not depend on the launch shape.
+        if constexpr (sizeof(T) == 4) {
+          const int hw = tid >> 4, hl = tid & 15;
+          for (int i0 = 0; i0 < NE; i0 += NT / 16) {
+            const int i = i0 + hw;
+            T sr = T(0), s1 = T(0);
+            if (i < NE) {
+              const T ka = kaS[i];
+              for (int ang = hl; ang < NA; ang += 16) {
+                const int q = i * NA + ang;
+                const T dom = S.dOm[ang];
+                sr += dom * RD[q];
+                s1 += dom * ID[q] * (T(1) + ka * S.taus[ang]);
+              }
+            }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_down_sync(0xffffffffu, sr, o);
-            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+            for (int o = 8; o > 0; o >>= 1) {
+              sr += __shfl_down_sync(0xffffffffu, sr, o, 16);
+              s1 += __shfl_down_sync(0xffffffffu, s1, o, 16);
+            }
+            if (hl == 0 && i < NE) S.rowJ[i] = sr / s1;
           }
-          if (lane == 0) S.rowJ[i] = sr / s1;
+        } else {
+          for (int i = warp; i < NE; i += (NT / 32)) {
+            T sr = T(0), s1 = T(0);
+            const T ka = kaS[i];
+            for (int ang = lane; ang < NA; ang += 32) {
+              const int q = i * NA + ang;
+              const T dom = S.dOm[ang];
+              sr += dom * RD[q];
+              s1 += dom * ID[q] * (T(1) + ka * S.taus[ang]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              sr += __shfl_down_sync(0xffffffffu, sr, o);
+              s1 += __shfl_down_sync(0xffffffffu, s1, o);
+            }
+            if (lane == 0) S.rowJ[i] = sr / s1;
+          }
         }
         __syncthreads();
       }
