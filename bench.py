@@ -154,8 +154,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (207.70e6 + 1080.02e6 + 1343.84e6 + 212.98e6,
-         "3b005c99538126eae2efd4b6208a92118038e331e43108b1f74575dcb57f8dc2"),
+        (208.30e6 + 1079.68e6 + 1343.23e6 + 213.29e6,
+         "66e714065ec8e1e4aea82c38d28894f52b7261fc94a6273a118ebec40c77eb44"),
 }
 
 
