@@ -352,7 +352,11 @@ static bool valid_shape(int nt) {
   return nt == 128 || nt == 256 || nt == 512 || nt == (bt::kShapeSplit | 256) || nt == (bt::kShapeSplit | 512);
 }
 static bool shape_fits(const bt_handle* h, int nt) {
-  return (long)bt::flux_smem_bytes(h->tb, h->mixed, nt) <= (long)bt::max_optin_smem() &&
+  // the flux kernels give each angle of a row its own thread (a CTA of fewer
+  // threads than angles would leave angles out)
+  const int threads = nt & ~bt::kShapeSplit;
+  return threads >= h->tb.n_ang &&
+         (long)bt::flux_smem_bytes(h->tb, h->mixed, nt) <= (long)bt::max_optin_smem() &&
          bt::flux_occupancy(h->tb, h->mixed, nt) > 0;
 }
 

@@ -260,3 +260,18 @@ def test_gpu_size_limits(gpu):
     with pytest.raises(gpu.BtError) as e:
         gpu.Transport(q, "fp64")
     assert e.value.code == -1 and "shared memory" in str(e.value)
+
+
+def test_launch_shapes_cover_every_angle(orc, gpu):
+    # 192 angles: a 128-thread CTA would leave angles without a thread, so
+    # that shape is refused and the autotuner does not consider it
+    p = W.random_column(19, n_r=6, n_e=3, n_mu=16, n_phi=12, n_s=1)
+    t = gpu.Transport(p, "fp64")
+    with pytest.raises(gpu.BtError) as e:
+        t.set_launch_shape(128)
+    assert e.value.code == -1
+    t.set_launch_shape(256)
+    t.set_background(p.backgrounds[0])
+    t.set_f(p.f0)
+    assert t.autotune(0.01) & 0xffff >= 192
+    o, t2, dt = compare_run(orc, gpu, p, 4)
