@@ -181,8 +181,12 @@ int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launche
  * which every face is computed once (by the zone that owns it) and writes both
  * neighbours' deposits, then a zone pass that gathers a zone's deposits in
  * the fused order and solves its collision; it needs 6 x the f array in
- * deposit rows, allocated when the shape is set.  Results are bitwise the same
- * for every shape. */
+ * deposit rows, allocated when the shape is set.  A shape needs at least one
+ * thread per angle bin (threads >= n_mu * n_phi); one that does not fit the
+ * problem (threads, shared memory, registers) is refused with BT_ERR_ARG and
+ * is not tried by the autotuner.  FP64 results are bitwise the same for
+ * every shape; mixed-precision results agree to float32 rounding (their
+ * exact-total sums are formed in a shape-dependent order). */
 #define BT_SHAPE_SPLIT 0x10000
 int bt_launch_shape(const bt_handle* h, int* threads_per_cta);
 int bt_set_launch_shape(bt_handle* h, int threads_per_cta);
