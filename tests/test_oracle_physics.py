@@ -107,6 +107,32 @@ def test_conservation_static_curved_moving(orc):
     assert np.allclose(E + Eo, E0, rtol=1e-13, atol=0)
 
 
+def test_conservation_with_shifts_of_several_groups(orc):
+    # group ratio 1.06: the moving, curved column's remaps move content by
+    # several groups at once (the energy weights' brackets m far from 0);
+    # with the content kept away from the clamped ends, number is conserved
+    # to round-off, which a wrong bracket, a lost rescaling of the content
+    # between groups of different width or a dropped tap would break
+    p = W.random_column(5, n_r=10, n_e=60, n_mu=6, n_phi=4, n_s=1, moving=True, gr=True)
+    p.eps_edges = np.geomspace(1.0, 1.06 ** 60, 61)
+    p = _scattering_only(p, 3)
+    keep = np.zeros(60, bool)
+    keep[28:32] = True
+    p.f0[:, :, ~keep, :] = 0.0
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    N0 = o.totals()[0]
+    dt = o.max_dt(0.5)
+    for _ in range(3):
+        o.step(dt)
+    N, E, No, Eo = o.totals()
+    occupied = np.nonzero(np.abs(o.get_f()).sum(axis=(0, 1, 3)))[0]
+    assert occupied.min() > 0 and occupied.max() < 59      # the ends were not reached
+    assert occupied.max() - occupied.min() > 12            # content moved by many groups
+    assert np.allclose(N + No, N0, rtol=1e-13, atol=0)
+
+
 def test_time_remap_conserves_number(orc):
     # alternating moving/curved backgrounds with no transport change
     p = W.random_column(7, n_r=6, n_e=5, n_mu=4, n_phi=4, n_s=2)
