@@ -111,8 +111,10 @@ def test_conservation_with_shifts_of_several_groups(orc):
     # group ratio 1.06: the moving, curved column's remaps move content by
     # several groups at once (the energy weights' brackets m far from 0);
     # with the content kept away from the clamped ends, number is conserved
-    # to round-off, which a wrong bracket, a lost rescaling of the content
-    # between groups of different width or a dropped tap would break
+    # to round-off: each source bin's content is split among its destination
+    # bins with weights summing to one, which a dropped or misplaced tap, or
+    # a deposit outside the grid, would break (the brackets themselves are
+    # pinned by test_weights_reproduce_target)
     p = W.random_column(5, n_r=10, n_e=60, n_mu=6, n_phi=4, n_s=1, moving=True, gr=True)
     p.eps_edges = np.geomspace(1.0, 1.06 ** 60, 61)
     p = _scattering_only(p, 3)
