@@ -142,7 +142,12 @@ int bt_get_f(bt_handle* h, int mem, void* f);
  * content through its faces in one step. */
 int bt_max_dt(bt_handle* h, double cfl, double* dt_out);
 
-/* One transport step of length dt (Sec. 3.3 Eq. fullstep, Sec. 3.5). */
+/* One transport step of length dt (Sec. 3.3 Eq. fullstep, Sec. 3.5).  The
+ * step is only enqueued: BT_OK means the launches were accepted.  A
+ * non-finite result (BT_ERR_NUMERIC) or a bounded device wait that gave up
+ * (BT_ERR_TIMEOUT) is recorded in device flags and reported by the next call
+ * that synchronises the stream and returns data (bt_get_f, bt_moments,
+ * bt_totals, bt_sur_stats, bt_autotune). */
 int bt_step(bt_handle* h, double dt);
 
 /* Collision source terms of the last step (Eq. hydrosource), per unit
@@ -195,8 +200,13 @@ int bt_set_launch_shape(bt_handle* h, int threads_per_cta);
  * set) for every launch shape that fits, keeps the fastest, and -- if the
  * environment variable BT_TUNE_CACHE names a file -- records it there under a
  * key of the problem shape; bt_create reads that file.  The timing launches
- * overwrite the last-step moments but not f.  The split shapes are tried
- * only if their deposit rows can be allocated.  *chosen_nt may be NULL. */
+ * leave f, the cumulative outflow and the last step's moments (bt_moments)
+ * as they were: the moments are copied aside before the trials and restored
+ * after them.  The split shapes are tried only if their deposit rows can be
+ * allocated.  *chosen_nt may be NULL.
+ * Without a cached choice, bt_create starts with the first of fused/256,
+ * split/256, split/512, fused/512, fused/128 that fits the problem; it
+ * refuses the problem (BT_ERR_ARG, "shared memory") only if none does. */
 int bt_autotune(bt_handle* h, double dt, int* chosen_nt);
 
 /* Batched step: n independent problems (each its own configuration, e.g. of

@@ -5,7 +5,8 @@ benchmark's CPU-baseline leg are the only callers.  The product library never
 imports this package, and this package imports nothing from the product
 library; both consume the seeded inputs of ``paper_2003_02845_gb300.workloads``.
 
-``build()`` compiles ``bt_oracle.c`` with gcc into ``oracle/_build``.
+``build()`` compiles ``bt_oracle.c`` with gcc (OpenMP) into ``oracle/_build``;
+``set_threads`` picks the number of threads, which does not change results.
 """
 from __future__ import annotations
 
@@ -28,7 +29,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_OUT, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -57,6 +58,11 @@ def lib():
         L.orc_grid.argtypes = [p, dp, dp, dp, dp, dp]
         L.orc_tir_count.restype = i
         L.orc_tir_count.argtypes = [p]
+        L.orc_clamp_counts.argtypes = [p, C.POINTER(C.c_long)]
+        L.orc_set_threads.argtypes = [i]
+        L.orc_threads.restype = i
+        L.orc_face_flux.restype = i
+        L.orc_face_flux.argtypes = [p, i, i, d, dp, dp]
         L.orc_gauss_legendre.argtypes = [i, dp, dp]
         L.orc_triad.argtypes = [d, d, dp]
         L.orc_rotation.argtypes = [d, d, d, d, dp]
@@ -83,6 +89,16 @@ def lib():
         L.orc_sur_samples.argtypes = [p, C.c_long, ip, dp, dp, ip]
         _lib = L
     return _lib
+
+
+def set_threads(n: int):
+    """Threads of the oracle's parallel loops (its results do not depend on
+    the number)."""
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
 
 
 def _dp(a: np.ndarray):
@@ -273,6 +289,23 @@ class Oracle:
 
     def tir_count(self) -> int:
         return lib().orc_tir_count(self.h)
+
+    def clamp_counts(self):
+        """(energy, mu) clamps of the remaps so far: deposits whose energy
+        target lay past the end groups, source bins whose mu target lay past
+        the outermost node (reading R-7)."""
+        c = (C.c_long * 2)()
+        lib().orc_clamp_counts(self.h, c)
+        return int(c[0]), int(c[1])
+
+    def face_flux(self, q: int, s: int, dt: float):
+        """Flux content [group][angle] of face q of the step's face list for
+        species s over dt, from the current f, and the face area."""
+        out = np.zeros((self.prob.n_eps, self.prob.n_ang))
+        area = C.c_double()
+        if not lib().orc_face_flux(self.h, int(q), int(s), float(dt), _dp(out), C.byref(area)):
+            raise IndexError("face %d" % q)
+        return out, area.value
 
     def sur_samples(self, idx):
         """Learned-remap rows idx [n][3] = (zone, kind, source angle):

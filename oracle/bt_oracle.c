@@ -18,10 +18,20 @@
  *
  * Parity: every function is pinned by the CPU test-suite against closed
  * forms, textbook special cases or brute force (see tests/test_oracle_*.py).
+ *
+ * Threads (OpenMP, when built with it): the faces of a step are taken in
+ * blocks; within a block every face's flux and its two remapped deposits
+ * are computed in parallel into buffers of their own, then added to the
+ * zones' content changes one face after another in face-list order.  The
+ * time remap and the collision solve are independent per zone.  Results are
+ * therefore the same bit for bit for any number of threads.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PI_ 3.14159265358979323846
 
@@ -361,6 +371,10 @@ typedef struct {
   double *dN, *dE, *dP;        /* [s][zone], [s][zone], [s][zone][3] */
   double *N_out, *E_out;       /* [s] cumulative outflow through open boundaries */
   int n_tir;
+  /* [R-7] diagnostics: deposits whose energy target lay past the first or
+   * last group (clamped into it), and source bins whose mu target lay past
+   * the outermost node */
+  long n_clamp_e, n_clamp_mu;
 } orc_t;
 
 static int nz(const orc_t *o) { return o->n_r * o->n_th; }
@@ -490,16 +504,18 @@ typedef struct { double th, ph; double v[3]; double al, cf; } loc_t;
 static void remap(orc_t *o, const loc_t *X, const loc_t *Y, int axis,
                   const double *src, double *dst, double scale) {
   double G[9];
+  long n_tir = 0, n_ce = 0, n_cm = 0;   /* diagnostics of this call */
   orc_rotation(X->th, X->ph, Y->th, Y->ph, G);
   for (int ang = 0; ang < o->n_ang; ++ang) {
     double n[3], rho, mus, Phis;
     bin_dir(o, ang, n);
-    o->n_tir += orc_chain(X->v, X->al, X->cf, Y->v, Y->al, Y->cf, G, axis, n, &rho, &mus, &Phis);
+    n_tir += orc_chain(X->v, X->al, X->cf, Y->v, Y->al, Y->cf, G, axis, n, &rho, &mus, &Phis);
     int m, jL, kL;
     double we, wm, wp;
     orc_weights_eps(rho, o->R, &m, &we);
     orc_weights_mu(mus, o->n_mu, o->mu, &jL, &wm);
     orc_weights_phi(Phis, o->n_ph, &kL, &wp);
+    if (o->n_mu > 1 && (mus <= o->mu[0] || mus >= o->mu[o->n_mu-1])) n_cm++;
     int jR = o->n_mu > 1 ? jL + 1 : jL;
     int kR = (kL + 1) % o->n_ph;
     for (int i = 0; i < o->n_e; ++i) {
@@ -507,9 +523,10 @@ static void remap(orc_t *o, const loc_t *X, const loc_t *Y, int axis,
       if (c == 0.0) continue;
       for (int ie = 0; ie < 2; ++ie) {
         int it = i + m + ie;
+        double w1 = ie ? we : 1.0 - we;
+        if ((it < 0 || it > o->n_e - 1) && w1 != 0.0) n_ce++;
         if (it < 0) it = 0;
         if (it > o->n_e - 1) it = o->n_e - 1;
-        double w1 = ie ? we : 1.0 - we;
         for (int ij = 0; ij < 2; ++ij) {
           int jt = ij ? jR : jL;
           double w2 = ij ? wm : 1.0 - wm;
@@ -522,6 +539,18 @@ static void remap(orc_t *o, const loc_t *X, const loc_t *Y, int axis,
       }
     }
   }
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+  o->n_tir += (int)n_tir;
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+  o->n_clamp_e += n_ce;
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+  o->n_clamp_mu += n_cm;
 }
 
 /* density of bin content per coordinate volume: phi^6 u^0 dGamma dOmega f
@@ -799,15 +828,20 @@ static void face_flux(orc_t *o, const face_t *F, int s, double dt, double *flux)
   for (int k = 0; k < 4; ++k) free(g[k]);
 }
 
-/* Deposit one face's flux into both neighbours' content changes
- * (Eq. fullstep): dN_P -= T_{s->P}[F], dN_Q += T_{s->Q}[F].  [R-13] */
-static void face_deposit(orc_t *o, const face_t *F, int s, const double *flux, double *dN) {
+/* Deposits of one face's flux into its two neighbours' content changes
+ * (Eq. fullstep): depP = -T_{s->P}[F], depQ = +T_{s->Q}[F], into zeroed
+ * buffers of their own; tally[0..1] = the number and the energy at infinity
+ * (alpha eps u^0 per unit number) that left through an open boundary.
+ * [R-13] */
+static void face_deposit(orc_t *o, const face_t *F, const double *flux, double *depP, double *depQ,
+                         double *tally) {
   size_t R = nrow(o);
-  int Z = nz(o);
-  if (F->z[1] >= 0) remap(o, &F->S, &F->L[1], F->axis, flux, dN + ((size_t)s*Z + F->z[1])*R, -1.0);
-  if (F->z[2] >= 0) remap(o, &F->S, &F->L[2], F->axis, flux, dN + ((size_t)s*Z + F->z[2])*R, +1.0);
+  memset(depP, 0, sizeof(double) * R);
+  memset(depQ, 0, sizeof(double) * R);
+  if (F->z[1] >= 0) remap(o, &F->S, &F->L[1], F->axis, flux, depP, -1.0);
+  if (F->z[2] >= 0) remap(o, &F->S, &F->L[2], F->axis, flux, depQ, +1.0);
+  tally[0] = tally[1] = 0.0;
   if (F->type == FACE_OUTFLOW_P || F->type == FACE_OUTFLOW_Q) {
-    /* outflow tallies: number, and energy at infinity alpha eps u^0 */
     double sg = F->type == FACE_OUTFLOW_P ? 1.0 : -1.0;
     for (int ang = 0; ang < o->n_ang; ++ang) {
       double n[3];
@@ -815,8 +849,8 @@ static void face_deposit(orc_t *o, const face_t *F, int s, const double *flux, d
       double u0 = u0_of(F->S.v, n);
       for (int i = 0; i < o->n_e; ++i) {
         double c = sg * flux[(size_t)i*o->n_ang + ang];
-        o->N_out[s] += c;
-        o->E_out[s] += c * F->S.al * o->e_c[i] * u0;
+        tally[0] += c;
+        tally[1] += c * F->S.al * o->e_c[i] * u0;
       }
     }
   }
@@ -828,22 +862,31 @@ static void face_deposit(orc_t *o, const face_t *F, int s, const double *flux, d
 static void time_remap(orc_t *o) {
   int Z = nz(o);
   size_t R = nrow(o);
-  double *d = (double *)malloc(sizeof(double) * R);
-  double *D = (double *)malloc(sizeof(double) * R);
-  for (int s = 0; s < o->n_s; ++s)
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+  {
+    double *d = (double *)malloc(sizeof(double) * R);
+    double *D = (double *)malloc(sizeof(double) * R);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
     for (int z = 0; z < Z; ++z) {
       loc_t X, Y;
       X.th = Y.th = 0.0; X.ph = Y.ph = 0.0;
       for (int m = 0; m < 3; ++m) { X.v[m] = o->v0[3*z+m]; Y.v[m] = o->v[3*z+m]; }
       X.al = o->al0[z]; X.cf = o->ph0[z];
       Y.al = o->al[z]; Y.cf = o->ph[z];
-      double *f = o->f + ((size_t)s*Z + z)*R;
-      to_density(o, &X, f, d);
-      memset(D, 0, sizeof(double) * R);
-      remap(o, &X, &Y, KICK_TIME, d, D, 1.0);
-      from_density(o, &Y, D, f);
+      for (int s = 0; s < o->n_s; ++s) {
+        double *f = o->f + ((size_t)s*Z + z)*R;
+        to_density(o, &X, f, d);
+        memset(D, 0, sizeof(double) * R);
+        remap(o, &X, &Y, KICK_TIME, d, D, 1.0);
+        from_density(o, &Y, D, f);
+      }
     }
-  free(d); free(D);
+    free(d); free(D);
+  }
 }
 
 /* enumerate every face once: returns the number written to `faces` */
@@ -873,6 +916,8 @@ static int build_faces(orc_t *o, face_t **out) {
 /*  3. f* = f^n + dN / (phi^6 dV u^0 dGamma dOmega)                         */
 /*  4. implicit collision per (zone, group) -> f^{n+1}; collision moments    */
 /* ------------------------------------------------------------------------- */
+enum { FACE_BLOCK = 256 };   /* faces whose deposits are computed together */
+
 static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
   int Z = nz(o);
   size_t R = nrow(o);
@@ -880,63 +925,100 @@ static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
   face_t *faces;
   int nf = build_faces(o, &faces);
   double *dN = (double *)calloc((size_t)o->n_s * Z * R, sizeof(double));
-  double *flux = (double *)malloc(sizeof(double) * R);
+  double *flux = (double *)malloc(sizeof(double) * R * FACE_BLOCK);
+  double *depP = (double *)malloc(sizeof(double) * R * FACE_BLOCK);
+  double *depQ = (double *)malloc(sizeof(double) * R * FACE_BLOCK);
+  double tally[2 * FACE_BLOCK];
+  int act[FACE_BLOCK];
   for (int s = 0; s < o->n_s; ++s)
-    for (int q = 0; q < nf; ++q) {
-      if (sel) {  /* subset mode: only faces that touch a selected zone */
-        int zp = faces[q].z[1], zq = faces[q].z[2];
-        if (!((zp >= 0 && sel[zp]) || (zq >= 0 && sel[zq]))) continue;
-      }
-      face_flux(o, &faces[q], s, dt, flux);
-      face_deposit(o, &faces[q], s, flux, dN);
-    }
-  free(flux);
-  double *r = (double *)malloc(sizeof(double) * o->n_ang);
-  double *tau = (double *)malloc(sizeof(double) * o->n_ang);
-  double *fst = (double *)malloc(sizeof(double) * o->n_ang);
-  double *fnew = (double *)malloc(sizeof(double) * o->n_ang);
-  double *u0 = (double *)malloc(sizeof(double) * o->n_ang);
-  double *nd = (double *)malloc(sizeof(double) * 3 * o->n_ang);
-  for (int z = 0; z < Z; ++z) {
-    if (sel && !sel[z]) continue;
-    loc_t X;
-    zone_loc(o, z, 0.0, 0.0, &X);
-    for (int ang = 0; ang < o->n_ang; ++ang) {
-      bin_dir(o, ang, nd + 3*ang);
-      u0[ang] = u0_of(X.v, nd + 3*ang);
-      tau[ang] = X.al * dt / u0[ang];       /* [R-17] */
-    }
-    double c6 = pow(X.cf, 6);
-    for (int s = 0; s < o->n_s; ++s) {
-      double sN = 0.0, sE = 0.0, sP[3] = {0, 0, 0};
-      for (int i = 0; i < o->n_e; ++i) {
-        size_t zo = ((size_t)s*Z + z)*o->n_e + i;
-        double ka = o->ka[zo], ks = o->ks[zo], fe = o->fe[zo];
-        size_t base = ((size_t)s*Z + z)*R + (size_t)i*o->n_ang;
-        const double *f = o->f + base;
-        const double *dn = dN + base;
-        for (int ang = 0; ang < o->n_ang; ++ang) {
-          fst[ang] = f[ang] + dn[ang] / (c6 * o->vol[z] * u0[ang] * o->dGam[i] * o->dOm[ang]);
-          r[ang] = fst[ang] + tau[ang]*ka*fe;
+    for (int q0 = 0; q0 < nf; q0 += FACE_BLOCK) {
+      int nb = nf - q0 < FACE_BLOCK ? nf - q0 : FACE_BLOCK;
+      /* the block's fluxes and deposits, each face on its own buffers */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+      for (int k = 0; k < nb; ++k) {
+        const face_t *F = &faces[q0 + k];
+        act[k] = 1;
+        if (sel) {  /* subset mode: only faces that touch a selected zone */
+          int zp = F->z[1], zq = F->z[2];
+          if (!((zp >= 0 && sel[zp]) || (zq >= 0 && sel[zq]))) { act[k] = 0; continue; }
         }
-        orc_collision_row(o->n_ang, r, tau, ka, ks, o->dOm, fnew);
-        double *dst = sel ? out + base : o->f + base;
-        for (int ang = 0; ang < o->n_ang; ++ang) {
-          /* collision moments (Eq. hydrosource) [R-17]: content change per
-           * coordinate volume and time */
-          double dc = c6 * u0[ang] * o->dGam[i] * o->dOm[ang] * (fnew[ang] - fst[ang]) / dt;
-          sN += dc;
-          sE += dc * o->e_c[i];
-          for (int m = 0; m < 3; ++m) sP[m] += dc * o->e_c[i] * nd[3*ang+m];
-          dst[ang] = fnew[ang];
+        face_flux(o, F, s, dt, flux + (size_t)k * R);
+        face_deposit(o, F, flux + (size_t)k * R, depP + (size_t)k * R, depQ + (size_t)k * R, tally + 2 * k);
+      }
+      /* added to the zones in face-list order */
+      for (int k = 0; k < nb; ++k) {
+        if (!act[k]) continue;
+        const face_t *F = &faces[q0 + k];
+        for (int side = 1; side <= 2; ++side) {
+          if (F->z[side] < 0) continue;
+          double *d = dN + ((size_t)s*Z + F->z[side])*R;
+          const double *src = (side == 1 ? depP : depQ) + (size_t)k * R;
+          for (size_t q = 0; q < R; ++q) d[q] += src[q];
+        }
+        if (F->type == FACE_OUTFLOW_P || F->type == FACE_OUTFLOW_Q) {
+          o->N_out[s] += tally[2 * k];
+          o->E_out[s] += tally[2 * k + 1];
         }
       }
-      o->dN[(size_t)s*Z + z] = sN;
-      o->dE[(size_t)s*Z + z] = sE;
-      for (int m = 0; m < 3; ++m) o->dP[((size_t)s*Z + z)*3 + m] = sP[m];
     }
+  free(flux); free(depP); free(depQ);
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+  {
+    double *r = (double *)malloc(sizeof(double) * o->n_ang);
+    double *tau = (double *)malloc(sizeof(double) * o->n_ang);
+    double *fst = (double *)malloc(sizeof(double) * o->n_ang);
+    double *fnew = (double *)malloc(sizeof(double) * o->n_ang);
+    double *u0 = (double *)malloc(sizeof(double) * o->n_ang);
+    double *nd = (double *)malloc(sizeof(double) * 3 * o->n_ang);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+    for (int z = 0; z < Z; ++z) {
+      if (sel && !sel[z]) continue;
+      loc_t X;
+      zone_loc(o, z, 0.0, 0.0, &X);
+      for (int ang = 0; ang < o->n_ang; ++ang) {
+        bin_dir(o, ang, nd + 3*ang);
+        u0[ang] = u0_of(X.v, nd + 3*ang);
+        tau[ang] = X.al * dt / u0[ang];       /* [R-17] */
+      }
+      double c6 = pow(X.cf, 6);
+      for (int s = 0; s < o->n_s; ++s) {
+        double sN = 0.0, sE = 0.0, sP[3] = {0, 0, 0};
+        for (int i = 0; i < o->n_e; ++i) {
+          size_t zo = ((size_t)s*Z + z)*o->n_e + i;
+          double ka = o->ka[zo], ks = o->ks[zo], fe = o->fe[zo];
+          size_t base = ((size_t)s*Z + z)*R + (size_t)i*o->n_ang;
+          const double *f = o->f + base;
+          const double *dn = dN + base;
+          for (int ang = 0; ang < o->n_ang; ++ang) {
+            fst[ang] = f[ang] + dn[ang] / (c6 * o->vol[z] * u0[ang] * o->dGam[i] * o->dOm[ang]);
+            r[ang] = fst[ang] + tau[ang]*ka*fe;
+          }
+          orc_collision_row(o->n_ang, r, tau, ka, ks, o->dOm, fnew);
+          double *dst = sel ? out + base : o->f + base;
+          for (int ang = 0; ang < o->n_ang; ++ang) {
+            /* collision moments (Eq. hydrosource) [R-17]: content change per
+             * coordinate volume and time */
+            double dc = c6 * u0[ang] * o->dGam[i] * o->dOm[ang] * (fnew[ang] - fst[ang]) / dt;
+            sN += dc;
+            sE += dc * o->e_c[i];
+            for (int m = 0; m < 3; ++m) sP[m] += dc * o->e_c[i] * nd[3*ang+m];
+            dst[ang] = fnew[ang];
+          }
+        }
+        o->dN[(size_t)s*Z + z] = sN;
+        o->dE[(size_t)s*Z + z] = sE;
+        for (int m = 0; m < 3; ++m) o->dP[((size_t)s*Z + z)*3 + m] = sP[m];
+      }
+    }
+    free(r); free(tau); free(fst); free(fnew); free(u0); free(nd);
   }
-  free(r); free(tau); free(fst); free(fnew); free(u0); free(nd); free(dN); free(faces);
+  free(dN); free(faces);
 }
 
 int orc_step(orc_t *o, double dt) {
@@ -1060,6 +1142,40 @@ void orc_grid(const orc_t *o, double *eps_c, double *dgam, double *mu, double *d
   memcpy(vol, o->vol, sizeof(double) * nz(o));
 }
 int orc_tir_count(const orc_t *o) { return o->n_tir; }
+
+/* threads of the parallel loops (OpenMP builds; 1 otherwise) */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+void orc_clamp_counts(const orc_t *o, long *out) { out[0] = o->n_clamp_e; out[1] = o->n_clamp_mu; }
+
+/* Flux content flux[group][angle] of face q of the step's face list (in the
+ * order the step builds it: radial faces row by row, then polar, then the
+ * periodic faces) for species s and step dt, from the current f; *area gets
+ * the face area.  Returns 0 if q is out of range.  (Test access to the
+ * interface state of Sec. 3.3.) */
+int orc_face_flux(orc_t *o, int q, int s, double dt, double *flux, double *area) {
+  face_t *faces;
+  int nf = build_faces(o, &faces);
+  int ok = q >= 0 && q < nf && s >= 0 && s < o->n_s;
+  if (ok) {
+    face_flux(o, &faces[q], s, dt, flux);
+    *area = faces[q].area;
+  }
+  free(faces);
+  return ok;
+}
 
 /* ------------------------------------------------------------------------- */
 /* Learned-remap rows (test reference of the library's sample generator).    */

@@ -164,6 +164,11 @@ struct bt_handle {
   // split form of the flux step: deposit rows and records (lazily allocated)
   void* dep = nullptr;
   void* rec = nullptr;
+  // generation of the device buffers a captured step reads beyond the
+  // workspace (deposit rows, learned-remap table and network): bumped
+  // whenever one of them is allocated, freed or swapped, so that a batch
+  // graph captured with the old buffers is never replayed
+  uint64_t gen = 0;
   // learned remap (bt_set_surrogate)
   bt_surrogate* sur = nullptr;
   void* sur_tab = nullptr;                    // [zone][31][n_ang] weights
@@ -330,6 +335,7 @@ size_t bt_workspace_bytes(const bt_config* cfg) {
 static int ensure_split(bt_handle* h) {
   if (h->dep && h->rec) return BT_OK;
   cudaError_t e = cudaStreamSynchronize(h->stream);
+  ++h->gen;
   if (e == cudaSuccess && !h->dep) e = cudaMalloc(&h->dep, bt::split_dep_bytes(h->tb, h->mixed));
   if (e == cudaSuccess && !h->rec) e = cudaMalloc(&h->rec, bt::split_rec_bytes(h->tb));
   if (e != cudaSuccess) {
@@ -343,6 +349,7 @@ static int ensure_split(bt_handle* h) {
 }
 static void release_split(bt_handle* h) {
   if (!h->dep && !h->rec) return;
+  ++h->gen;
   cudaStreamSynchronize(h->stream);
   if (h->dep) cudaFree(h->dep);
   if (h->rec) cudaFree(h->rec);
@@ -546,17 +553,25 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
     if (pe) { bt_destroy(h); return cuda_fail((cudaError_t)pe, "cudaFuncSetAttribute"); }
   }
   h->tune_key = tune_key(c);
-  h->nt = 256;
+  // launch shape: the autotuner's cached choice if it fits, else the first
+  // of fused/256, split/256, split/512, fused/512, fused/128 that fits (the
+  // split form's passes need less shared memory per CTA than the fused one)
+  h->nt = 0;
   {
-    int cached = tune_lookup(h->tune_key);
-    if (valid_shape(cached) && shape_fits(h, cached) &&
-        (!(cached & bt::kShapeSplit) || ensure_split(h) == BT_OK))
-      h->nt = cached;
+    const int S = bt::kShapeSplit;
+    const int order[6] = {tune_lookup(h->tune_key), 256, S | 256, S | 512, 512, 128};
+    for (int nt : order) {
+      if (!valid_shape(nt) || !shape_fits(h, nt)) continue;
+      if ((nt & S) && ensure_split(h) != BT_OK) continue;
+      h->nt = nt;
+      break;
+    }
   }
   // shared memory per CTA must fit the opt-in limit
-  size_t need = std::max(bt::flux_smem_bytes(T, h->mixed, h->nt), bt::remap_smem_bytes(T, h->mixed));
   int lim = bt::max_optin_smem();
-  if ((long)need > (long)lim) {
+  size_t need = bt::remap_smem_bytes(T, h->mixed);
+  if (h->nt == 0) need = std::max(need, bt::flux_smem_bytes(T, h->mixed, 256));
+  if (h->nt == 0 || (long)need > (long)lim) {
     bt_destroy(h);
     return fail(BT_ERR_ARG, "problem needs " + std::to_string(need) + " bytes of shared memory per CTA (limit " +
                                 std::to_string(lim) + ")");
@@ -756,6 +771,32 @@ int bt_autotune(bt_handle* h, double dt, int* chosen_nt) {
   const int cand[5] = {128, 256, 512, S | 256, S | 512};
   float best = 0.f;
   int best_nt = h->nt;
+  // the trial launches write the per-zone moments and outflow of a step that
+  // is never taken: keep the last step's copies and put them back afterwards
+  const size_t nsz = (size_t)h->cfg.n_species * h->nzone;
+  struct Keep { void* buf; size_t bytes; } keep[6] = {
+      {h->st.mom_N, 8 * nsz}, {h->st.mom_E, 8 * nsz}, {h->st.mom_P, 8 * 3 * nsz},
+      {h->st.out_N, 8 * nsz}, {h->st.out_E, 8 * nsz}, {h->qye, 8 * h->nzone}};
+  size_t keep_bytes = 0;
+  for (const Keep& k : keep) keep_bytes += k.bytes;
+  char* saved = nullptr;
+  {
+    cudaError_t ce = cudaMallocAsync(reinterpret_cast<void**>(&saved), keep_bytes, h->stream);
+    if (ce != cudaSuccess) { cudaGetLastError(); return cuda_fail(ce, "autotune: moment copies"); }
+    size_t o = 0;
+    for (const Keep& k : keep) {
+      cudaMemcpyAsync(saved + o, k.buf, k.bytes, cudaMemcpyDeviceToDevice, h->stream);
+      o += k.bytes;
+    }
+  }
+  auto restore = [&]() {
+    size_t o = 0;
+    for (const Keep& k : keep) {
+      cudaMemcpyAsync(k.buf, saved + o, k.bytes, cudaMemcpyDeviceToDevice, h->stream);
+      o += k.bytes;
+    }
+    cudaFreeAsync(saved, h->stream);
+  };
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -771,17 +812,18 @@ int bt_autotune(bt_handle* h, double dt, int* chosen_nt) {
       return r;
     };
     int e = run();
-    if (e) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail((cudaError_t)e, "autotune"); }
+    if (e) { restore(); cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail((cudaError_t)e, "autotune"); }
     cudaEventRecord(a, h->stream);
     for (int k = 0; k < 3; ++k) run();
     cudaEventRecord(b, h->stream);
     cudaError_t ce = cudaEventSynchronize(b);
     float ms = 0.f;
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, b);
-    if (ce != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(ce, "autotune timing"); }
+    if (ce != cudaSuccess) { restore(); cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(ce, "autotune timing"); }
     h->launches += 4;
     if (best == 0.f || ms < best) { best = ms; best_nt = nt; }
   }
+  restore();
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->nt = best_nt;
@@ -893,6 +935,7 @@ int bt_set_surrogate(bt_handle* h, bt_surrogate* s, double tol) {
       return cuda_fail(e, "learned remap table");
     }
   }
+  ++h->gen;
   h->sur = s;
   h->sur_tol = (float)tol;
   return BT_OK;
@@ -996,6 +1039,7 @@ int bt_batch_step(bt_batch* b, const double* dt) {
     key.push_back(h->nt);
     key.push_back(h->sur ? 1.0 : 0.0);
     key.push_back(h->sur_tol);
+    key.push_back((double)h->gen);   // the buffers the graph would read
   }
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {

@@ -35,3 +35,24 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(bt, "_lib", None)
     with pytest.raises(RuntimeError):
         bt.lib()
+
+
+def test_noalloc_refuses_sizes_beyond_its_array():
+    # the allocation-free totals keep n_s * ceil(n_zone / 64) partials in a
+    # fixed device array; a larger request is refused on the host with
+    # BT_ERR_ARG before anything touches the device (the pointers are never
+    # dereferenced)
+    from paper_2003_02845_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    fn = lib.bt_weighted_totals_noalloc
+    vp, i32 = ctypes.c_void_p, ctypes.c_int
+    fn.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp, vp, vp]
+    fn.restype = i32
+    limit = 1 << 16
+    dummy = vp(16)
+    for n_s, n_zone in ((2, 64 * limit), (1, 64 * limit + 1), (limit + 1, 1)):
+        assert fn(dummy, 0, n_s, n_zone, 4, 8, dummy, dummy, dummy, None) == -1
+    # sizes, precision and pointers are checked the same way
+    assert fn(dummy, 0, 0, 1, 1, 1, dummy, dummy, dummy, None) == -1
+    assert fn(dummy, 7, 1, 1, 1, 1, dummy, dummy, dummy, None) == -1
+    assert fn(None, 0, 1, 1, 1, 1, dummy, dummy, dummy, None) == -1

@@ -226,8 +226,11 @@ def sphere_exact(r, R=1.0, ka=4.0, n=4000):
     return np.sum(mu * f) / np.sum(f), np.sum(mu * mu * f) / np.sum(f)
 
 
-def test_homogeneous_sphere_steady_state(orc):
-    tau = GOLDEN["radiating_sphere_setup"]["tau_low"]
+@pytest.mark.parametrize("which", ["tau_low", "tau_high"])
+def test_homogeneous_sphere_steady_state(orc, which):
+    # Sec. 4.1 runs the sphere at a low (tau = 4) and a high (tau = 26)
+    # optical depth; both must meet the paper's MSD bound on H/J and K/J
+    tau = GOLDEN["radiating_sphere_setup"][which]
     p = W.homogeneous_sphere(n_r=24, kappa=tau, n_e=1, n_mu=16, n_phi=4, dang=0.25)
     o = orc.Oracle(p)
     o.set_background(p.backgrounds[0])
