@@ -21,8 +21,8 @@
  * Conventions
  *   Units: c = 1; lengths and dt in the same length unit; kappa per length.
  *   Zones: zone = b * n_r + a (a radial, b polar).
- *   Angles: ang = j * n_phi + k (mu index j over Gauss-Legendre nodes in
- *           ascending order, Phi index k with centres (k + 1/2) 2pi/n_phi).
+ *   Angles: ang = j * n_phi + k (mu index j over the mu nodes in ascending
+ *           order, Phi index k with centres (k + 1/2) 2pi/n_phi).
  *   f layout: f[s][zone][group][ang], float64 (BT_FP64) or float32 (BT_MIXED).
  *   Opacity layout: [s][zone][group]; vectors [zone][3] as (r, theta, phi)
  *           components in the zone's local orthonormal triad.
@@ -62,6 +62,7 @@ enum { BT_GEOM_SPHERICAL = 0, BT_GEOM_SLAB = 1 };
 enum { BT_FP64 = 0, BT_MIXED = 1 };
 enum { BT_MEM_HOST = 0, BT_MEM_DEVICE = 1 };
 enum { BT_NUE = 0, BT_NUEBAR = 1, BT_NUX = 2 };
+enum { BT_GAUSS_LEGENDRE = 0, BT_GAUSS_LOBATTO = 1 };
 
 typedef struct bt_handle bt_handle;
 
@@ -80,7 +81,14 @@ typedef struct bt_handle bt_handle;
  *                 reflecting wall (spherical geometry).
  *  species_kind   n_species entries of BT_NUE/BT_NUEBAR/BT_NUX (host, copied).
  *  eps_edges      n_eps + 1 log-uniform group edges (constant ratio; host).
- *  n_mu, n_phi    angular grid: Gauss-Legendre mu cells x uniform Phi cells.
+ *  n_mu, n_phi    angular grid: n_mu mu cells x n_phi uniform Phi cells.
+ *  mu_quadrature  BT_GAUSS_LEGENDRE (0): mu nodes and cell widths are the
+ *                 Gauss-Legendre nodes and weights.  BT_GAUSS_LOBATTO: the
+ *                 Gauss-Lobatto ones (Sec. 3.1: cell widths equal to the
+ *                 Gauss-Lobatto weights; Sec. 5: mu = 1 as a collocation
+ *                 point), n_mu >= 2.  The nodes mu = -1 and +1 are then one
+ *                 direction each, held by n_phi cells; content the remap
+ *                 moves into such a pole node is spread evenly over its cells.
  *  precision      BT_FP64 or BT_MIXED (float32 f, fluxes and remap; float64
  *                 collision solve, content accumulators and sums).
  *  phase_norm     the 1/h^3 factor of the hydro source terms (Eq. hydrosource).
@@ -101,6 +109,7 @@ typedef struct bt_config {
   int32_t precision;
   double phase_norm;
   void* stream;
+  int32_t mu_quadrature;
 } bt_config;
 
 /* Message of the last failed call on this host thread (never NULL). */
@@ -177,6 +186,14 @@ int64_t bt_launch_count(const bt_handle* h);
 enum { BT_K_TIME_REMAP = 0, BT_K_FLUX = 1, BT_K_OUTFLOW = 2, BT_K_SUR_TABLE = 3, BT_K_ZONE = 4 };
 int bt_profile(bt_handle* h, int enable);
 int bt_profile_read(bt_handle* h, int kernel, double* total_ms, int64_t* launches);
+
+/* Measured fused multiply-add rate of the current device in the arithmetic
+ * of `precision` (BT_FP64: float64, BT_MIXED: float32), in flop/s (an FMA is
+ * two flops): independent FMA chains on every SM, timed with CUDA events on
+ * `stream` (cudaStream_t).  A measurement aid with no counterpart in the
+ * paper: it gives the ALU peak that the transport kernels' arithmetic is
+ * compared with.  Synchronises; BT_OK, BT_ERR_ARG or BT_ERR_CUDA. */
+int bt_peak_fma(int precision, double* flops_per_s, void* stream);
 
 /* Launch shape of the flux step.  128, 256 or 512: the fused form, one
  * kernel in which each zone's CTA computes all of its faces (every interior

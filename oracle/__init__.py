@@ -43,7 +43,7 @@ def lib():
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)
         L.orc_create.restype = p
-        L.orc_create.argtypes = [i, i, i, dp, i, d, d, i, ip, i, dp, i, i, d]
+        L.orc_create.argtypes = [i, i, i, dp, i, d, d, i, ip, i, dp, i, i, d, i]
         L.orc_destroy.argtypes = [p]
         L.orc_set_background.argtypes = [p, dp, dp, dp, dp, dp, dp]
         L.orc_set_f.argtypes = [p, dp]
@@ -64,6 +64,7 @@ def lib():
         L.orc_face_flux.restype = i
         L.orc_face_flux.argtypes = [p, i, i, d, dp, dp]
         L.orc_gauss_legendre.argtypes = [i, dp, dp]
+        L.orc_gauss_lobatto.argtypes = [i, dp, dp]
         L.orc_triad.argtypes = [d, d, dp]
         L.orc_rotation.argtypes = [d, d, d, d, dp]
         L.orc_boost.argtypes = [dp, i, dp, dp]
@@ -120,6 +121,13 @@ def gauss_legendre(n: int):
     x = np.zeros(n)
     w = np.zeros(n)
     lib().orc_gauss_legendre(n, _dp(x), _dp(w))
+    return x, w
+
+
+def gauss_lobatto(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().orc_gauss_lobatto(n, _dp(x), _dp(w))
     return x, w
 
 
@@ -223,7 +231,8 @@ class Oracle:
         self._keep += [r_e, e_e, kinds]
         self.h = L.orc_create(prob.geom, prob.n_r, prob.n_theta, _dp(r_e), int(prob.theta_periodic),
                               float(prob.dtheta_column), float(prob.dphi), prob.n_species, _ip(kinds),
-                              prob.n_eps, _dp(e_e), prob.n_mu, prob.n_phi, phase_norm)
+                              prob.n_eps, _dp(e_e), prob.n_mu, prob.n_phi, phase_norm,
+                              1 if getattr(prob, "mu_quadrature", "legendre") == "lobatto" else 0)
         self.shape = (prob.n_species, prob.n_zone, prob.n_eps, prob.n_ang)
 
     def close(self):

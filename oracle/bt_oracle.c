@@ -87,6 +87,43 @@ void orc_gauss_legendre(int n, double *x, double *w) {
   if (n % 2 == 1) x[n / 2] = 0.0;
 }
 
+/* Gauss-Lobatto nodes (ascending, x[0] = -1, x[n-1] = 1) and weights on
+ * [-1, 1], n >= 2: the interior nodes are the roots of P'_{n-1}, found by
+ * Newton's method on P'_{n-1} from the Chebyshev-Lobatto points, and
+ * w_i = 2 / (n (n-1) P_{n-1}(x_i)^2).
+ * [R-2] Sec. 3.1 asks for mu cells whose widths are the Gauss-Lobatto weights:
+ * node mu_j is the cell's direction (mu = +-1 among them), its weight the
+ * cell's width. */
+void orc_gauss_lobatto(int n, double *x, double *w) {
+  int N = n - 1;   /* degree of the Legendre polynomial */
+  x[0] = -1.0; x[N] = 1.0;
+  w[0] = w[N] = 2.0 / (n * (double)N);
+  for (int i = 1; i <= N / 2; ++i) {
+    /* i-th largest interior root of P'_N */
+    double z = cos(PI_ * i / N);
+    for (int it = 0; it < 100; ++it) {
+      /* P'_N and P''_N from P_N, P_{N-1}: (1-z^2) P'' = 2 z P' - N (N+1) P */
+      double p, dp;
+      legendre(N, z, &p, &dp);
+      double d2p = (2.0*z*dp - N*(N + 1.0)*p) / (1.0 - z*z);
+      double dz = dp / d2p;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double p, dp;
+    legendre(N, z, &p, &dp);
+    double wi = 2.0 / (n * (double)N * p * p);
+    x[N - i] = z;  x[i] = -z;
+    w[N - i] = wi; w[i] = wi;
+  }
+  if (n % 2 == 1) {   /* odd n: the centre node */
+    double p, dp;
+    legendre(N, 0.0, &p, &dp);
+    x[N / 2] = 0.0;
+    w[N / 2] = 2.0 / (n * (double)N * p * p);
+  }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Frames (Sec. 3.2.1): local orthonormal triad at colatitude th, azimuth ph  */
 /* E columns = (r_hat, theta_hat, phi_hat) in Cartesian components.          */
@@ -356,6 +393,7 @@ typedef struct {
   double dth_col, dphi;
   double *r_e, *th_e;
   int n_s, n_e, n_mu, n_ph, n_ang;
+  int lobatto;                 /* [R-2] mu cells on Gauss-Lobatto nodes (pole nodes mu = +-1) */
   int *kind;
   double *e_e, *e_c, *dGam, R;
   double *mu, *dmu, *Phc, *dOm;
@@ -384,8 +422,9 @@ static size_t nrow(const orc_t *o) { return (size_t)o->n_e * o->n_ang; }
  * eps_i = 3/4 (e+^4 - e-^4)/(e+^3 - e-^3);  dGamma_i = (e+^3 - e-^3)/3. */
 orc_t *orc_create(int geom, int n_r, int n_th, const double *r_edges, int periodic_th,
                   double dth_col, double dphi, int n_s, const int *kind,
-                  int n_e, const double *e_edges, int n_mu, int n_ph, double phase_norm) {
+                  int n_e, const double *e_edges, int n_mu, int n_ph, double phase_norm, int lobatto) {
   orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
+  o->lobatto = lobatto && n_mu >= 2;
   o->geom = geom; o->n_r = n_r; o->n_th = n_th; o->periodic_th = periodic_th;
   o->dth_col = dth_col; o->dphi = dphi; o->n_s = n_s; o->n_e = n_e;
   o->n_mu = n_mu; o->n_ph = n_ph; o->n_ang = n_mu * n_ph; o->phase_norm = phase_norm;
@@ -411,7 +450,8 @@ orc_t *orc_create(int geom, int n_r, int n_th, const double *r_edges, int period
   o->R = n_e > 1 ? o->e_c[1] / o->e_c[0] : 2.0;
   o->mu = (double *)malloc(sizeof(double) * n_mu);
   o->dmu = (double *)malloc(sizeof(double) * n_mu);
-  orc_gauss_legendre(n_mu, o->mu, o->dmu);
+  if (o->lobatto) orc_gauss_lobatto(n_mu, o->mu, o->dmu);
+  else orc_gauss_legendre(n_mu, o->mu, o->dmu);
   o->Phc = (double *)malloc(sizeof(double) * n_ph);
   for (int k = 0; k < n_ph; ++k) o->Phc[k] = (k + 0.5) * 2.0*PI_ / n_ph;
   o->dOm = (double *)malloc(sizeof(double) * o->n_ang);
@@ -515,7 +555,7 @@ static void remap(orc_t *o, const loc_t *X, const loc_t *Y, int axis,
     orc_weights_eps(rho, o->R, &m, &we);
     orc_weights_mu(mus, o->n_mu, o->mu, &jL, &wm);
     orc_weights_phi(Phis, o->n_ph, &kL, &wp);
-    if (o->n_mu > 1 && (mus <= o->mu[0] || mus >= o->mu[o->n_mu-1])) n_cm++;
+    if (o->n_mu > 1 && (mus < o->mu[0] || mus > o->mu[o->n_mu-1])) n_cm++;
     int jR = o->n_mu > 1 ? jL + 1 : jL;
     int kR = (kL + 1) % o->n_ph;
     for (int i = 0; i < o->n_e; ++i) {
@@ -530,6 +570,13 @@ static void remap(orc_t *o, const loc_t *X, const loc_t *Y, int axis,
         for (int ij = 0; ij < 2; ++ij) {
           int jt = ij ? jR : jL;
           double w2 = ij ? wm : 1.0 - wm;
+          if (o->lobatto && (jt == 0 || jt == o->n_mu - 1)) {
+            /* [R-2b] a pole node (mu = +-1): its N_Phi cells are one
+             * direction, so the content is spread evenly over them */
+            for (int kt = 0; kt < o->n_ph; ++kt)
+              dst[(size_t)it*o->n_ang + jt*o->n_ph + kt] += w1*w2*c / o->n_ph;
+            continue;
+          }
           for (int ik = 0; ik < 2; ++ik) {
             int kt = ik ? kR : kL;
             double w3 = ik ? wp : 1.0 - wp;

@@ -18,6 +18,7 @@ BT_OK = 0
 BT_GEOM_SPHERICAL, BT_GEOM_SLAB = 0, 1
 BT_FP64, BT_MIXED = 0, 1
 BT_MEM_HOST, BT_MEM_DEVICE = 0, 1
+BT_GAUSS_LEGENDRE, BT_GAUSS_LOBATTO = 0, 1
 SHAPE_SPLIT = 0x10000   # launch-shape flag of the split flux step
 
 _lib = None
@@ -32,6 +33,7 @@ class BtConfig(C.Structure):
         ("n_eps", C.c_int32), ("eps_edges", C.POINTER(C.c_double)),
         ("n_mu", C.c_int32), ("n_phi", C.c_int32), ("precision", C.c_int32),
         ("phase_norm", C.c_double), ("stream", C.c_void_p),
+        ("mu_quadrature", C.c_int32),
     ]
 
 
@@ -87,6 +89,7 @@ def lib():
         L.bt_batch_destroy.argtypes = [vp]
         L.bt_profile.argtypes = [vp, i32]
         L.bt_profile_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.bt_peak_fma.argtypes = [i32, C.POINTER(C.c_double), vp]
         L.bt_sur_samples.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
         L.bt_set_surrogate.argtypes = [vp, vp, C.c_double]
         L.bt_sur_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -143,6 +146,8 @@ def make_config(prob, precision: str, stream_handle: int, phase_norm: float = 1.
     cfg.precision = BT_MIXED if precision == "mixed" else BT_FP64
     cfg.phase_norm = phase_norm
     cfg.stream = stream_handle
+    cfg.mu_quadrature = BT_GAUSS_LOBATTO if getattr(prob, "mu_quadrature", "legendre") == "lobatto" \
+        else BT_GAUSS_LEGENDRE
     return cfg
 
 
@@ -442,6 +447,18 @@ class Surrogate:
         log = np.zeros(int(epochs), dtype=np.float32)
         _check(lib().bt_sur_train(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], C.byref(cfg), log.ctypes.data))
         return log
+
+
+def peak_fma(precision: str, stream=None) -> float:
+    """Measured FMA rate (flop/s) of the current GPU in float64 ("fp64") or
+    float32 ("mixed"), see bt_peak_fma."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    rc = lib().bt_peak_fma(BT_MIXED if precision == "mixed" else BT_FP64, C.byref(out), s.cuda_stream)
+    if rc != BT_OK:
+        raise BtError(rc, "bt_peak_fma failed")
+    return out.value
 
 
 def shape_name(nt: int) -> str:

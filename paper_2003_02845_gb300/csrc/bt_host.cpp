@@ -76,6 +76,51 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   if (n % 2 == 1) x[n / 2] = 0.0;
 }
 
+// Gauss-Lobatto nodes/weights (n >= 2): x = -1, 1 and the roots of
+// q(x) = P_{N-1}(x) - x P_N(x) (N = n - 1; q is proportional to
+// (1 - x^2) P_N'(x)), by Newton's method from the Chebyshev-Lobatto points;
+// weights 2 / (N (N + 1) P_N(x)^2).  Nodes mirrored to be exactly
+// antisymmetric.
+void gauss_lobatto(int n, std::vector<double>& x, std::vector<double>& w) {
+  const int N = n - 1;
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  x[0] = -1.0; x[N] = 1.0;
+  w[0] = w[N] = 2.0 / (N * (N + 1.0));
+  // P_{N-1}, P_N and their derivatives at z by the three-term recurrence
+  auto legendre2 = [N](double z, double& pN1, double& pN, double& dN1, double& dN) {
+    double p0 = 1.0, p1 = z, d0 = 0.0, d1 = 1.0;
+    for (int k = 2; k <= N; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      double d2 = d0 + (2.0 * k - 1.0) * p1;   // P_k' = P_{k-2}' + (2k-1) P_{k-1}
+      p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    }
+    pN1 = p0; pN = p1; dN1 = d0; dN = d1;
+  };
+  for (int i = 1; i <= N / 2; ++i) {
+    double z = std::cos(kPi * i / N);
+    double pN1, pN, dN1, dN;
+    for (int it = 0; it < 60; ++it) {
+      legendre2(z, pN1, pN, dN1, dN);
+      const double q = pN1 - z * pN;
+      const double dq = dN1 - pN - z * dN;
+      const double dz = q / dq;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-17) break;
+    }
+    legendre2(z, pN1, pN, dN1, dN);
+    const double wi = 2.0 / (N * (N + 1.0) * pN * pN);
+    x[N - i] = z; x[i] = -z;
+    w[N - i] = wi; w[i] = wi;
+  }
+  if (n % 2 == 1) {
+    double pN1, pN, dN1, dN;
+    legendre2(0.0, pN1, pN, dN1, dN);
+    x[N / 2] = 0.0;
+    w[N / 2] = 2.0 / (N * (N + 1.0) * pN * pN);
+  }
+}
+
 // local triad (r_hat, theta_hat, phi_hat) as columns, row-major E[3*m + c]
 void triad(double th, double ph, double E[9]) {
   double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
@@ -275,6 +320,9 @@ int validate(const bt_config* c) {
     }
   }
   if (c->precision != BT_FP64 && c->precision != BT_MIXED) return fail(BT_ERR_ARG, "precision");
+  if (c->mu_quadrature != BT_GAUSS_LEGENDRE && c->mu_quadrature != BT_GAUSS_LOBATTO)
+    return fail(BT_ERR_ARG, "mu_quadrature");
+  if (c->mu_quadrature == BT_GAUSS_LOBATTO && c->n_mu < 2) return fail(BT_ERR_ARG, "Gauss-Lobatto needs n_mu >= 2");
   return BT_OK;
 }
 
@@ -285,7 +333,8 @@ std::mutex g_tune_mutex;
 std::string tune_key(const bt_config* c) {
   std::ostringstream k;
   k << "v1|" << (c->precision == BT_MIXED ? "mixed" : "fp64") << "|g" << c->geom << "|s" << c->n_species << "|e"
-    << c->n_eps << "|mu" << c->n_mu << "|ph" << c->n_phi << "|z" << (long)c->n_r * c->n_theta;
+    << c->n_eps << "|mu" << c->n_mu << (c->mu_quadrature == BT_GAUSS_LOBATTO ? "L" : "") << "|ph" << c->n_phi
+    << "|z" << (long)c->n_r * c->n_theta;
   return k.str();
 }
 
@@ -403,7 +452,9 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   const bool slab = c->geom == BT_GEOM_SLAB;
   const double dph = slab ? 0.0 : c->dphi_wedge;
   std::vector<double> mu, wmu;
-  gauss_legendre(nmu, mu, wmu);
+  const bool lobatto = c->mu_quadrature == BT_GAUSS_LOBATTO;
+  if (lobatto) gauss_lobatto(nmu, mu, wmu);
+  else gauss_legendre(nmu, mu, wmu);
   std::vector<double> smu(nmu), cph(nph), sph(nph), dOm(nang), dGam(ne), eps(ne);
   for (int j = 0; j < nmu; ++j) smu[j] = std::sqrt(1.0 - mu[j] * mu[j]);
   for (int k = 0; k < nph; ++k) {
@@ -499,6 +550,7 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   T.inner_zero = !slab && r_e[0] == 0.0; T.inner_reflect = !slab && r_e[0] > 0.0;
   T.n_r = nr; T.n_th = nth; T.n_zone = (int)nz; T.n_s = c->n_species; T.n_e = ne;
   T.n_mu = nmu; T.n_ph = nph; T.n_ang = nang;
+  T.pole = lobatto && nph > 1;   // pole nodes whose Phi cells share one direction
   T.R = R; T.logR = std::log(R); T.dphi = dph; T.dth_col = T.periodic_th ? c->dtheta_column : 0.0;
   T.mu = D(P.tables[0]); T.smu = D(P.tables[1]); T.cph = D(P.tables[2]); T.sph = D(P.tables[3]);
   T.dOm = D(P.tables[4]); T.dGam = D(P.tables[5]); T.eps = D(P.tables[6]); T.vol = D(P.tables[7]);

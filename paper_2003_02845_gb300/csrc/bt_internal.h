@@ -19,10 +19,12 @@ enum Axis { AX_R = 0, AX_TH = 1, AX_PH = 2, AX_TIME = 3 };
 struct Tables {
   int geom, slab, periodic_th, inner_reflect, inner_zero;
   int n_r, n_th, n_zone, n_s, n_e, n_mu, n_ph, n_ang;
+  int pole;            // Gauss-Lobatto mu grid: nodes 0 and n_mu-1 are mu = -1, +1, whose
+                       // n_ph cells are one direction; remapped content is spread evenly over them
   double R;            // constant ratio of consecutive group centres
   double logR;
   double dphi, dth_col;
-  const double* mu;    // [n_mu] Gauss-Legendre nodes, ascending
+  const double* mu;    // [n_mu] Gauss-Legendre or Gauss-Lobatto nodes, ascending
   const double* smu;   // [n_mu] sqrt(1 - mu^2)
   const double* cph;   // [n_ph] cos Phi_k
   const double* sph;   // [n_ph] sin Phi_k

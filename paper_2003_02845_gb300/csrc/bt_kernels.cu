@@ -54,7 +54,6 @@ struct Loc {
   T v[3];
   T g, gg;   // gamma and gamma^2/(gamma+1)
   T al, cf;
-  T ral, rcf;   // 1/alpha, 1/phi (formed once per location)
 };
 
 template <typename T>
@@ -64,7 +63,6 @@ __device__ __forceinline__ void make_loc(Loc<T>& L, const double* v, double al, 
   L.g = T(1) / sqrt(T(1) - v2);
   L.gg = L.g * L.g / (L.g + T(1));
   L.al = (T)al; L.cf = (T)cf;
-  L.ral = T(1) / L.al; L.rcf = T(1) / L.cf;
 }
 
 template <typename T>
@@ -159,8 +157,15 @@ __device__ void chain_weights_dir(const Tables& tb, const T* s_mu, const T* n, c
                                   const T* G, int gT, int axis, const EBr<T>& K, Wt<T>& w) {
   T e, p[3];
   boost_fwd(X, n, e, p);
-  const T a = X.al * Y.ral;
-  const T cr = X.cf * Y.rcf;
+  // the metric ratios by correctly rounded divisions: where the metric is the
+  // same on both sides (periodic images, equal neighbours, flat regions)
+  // they are exactly 1.  A reciprocal then a product can round to 1 - ulp,
+  // and for a direction tangent to the face (normal component 0, e.g. the
+  // pole cells of a Gauss-Lobatto grid at polar and azimuthal faces) the
+  // kick's normal component sqrt(a^2 - b^2) |p_t| would then be sqrt(ulp)
+  // instead of 0.
+  const T a = X.al / Y.al;
+  const T cr = X.cf / Y.cf;
   const T bq = cr * cr;
   kick(axis, a, bq, e, p);
   if (G) {
@@ -342,6 +347,22 @@ template <typename T>
 struct AEnt {
   T w;     // angular weight wmu * wphi
   int b;   // source angle
+  __device__ __forceinline__ T weight() const { return w; }
+  __device__ __forceinline__ void set(T ww, int bb) { w = ww; b = bb; }
+};
+// float64 entries in 12 bytes (the weight's two 32-bit halves and the source
+// angle) instead of a 16-byte padded struct: six remaps' lists of the largest
+// rows then fit the float64 face pass in shared memory
+template <>
+struct AEnt<double> {
+  int lo, hi;
+  int b;
+  __device__ __forceinline__ double weight() const { return __hiloint2double(hi, lo); }
+  __device__ __forceinline__ void set(double ww, int bb) {
+    lo = __double2loint(ww);
+    hi = __double2hiint(ww);
+    b = bb;
+  }
 };
 
 // the angular targets of one source angle in four fixed slots (mu bracket
@@ -428,8 +449,7 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
       for (int w = 0; w < (b >> 5); ++w) pos += __popc(mt[w]);
       pos += __popc(mt[b >> 5] & ((1u << (b & 31)) - 1u));
       AEnt<T> e;
-      e.w = wa[k];
-      e.b = b;
+      e.set(wa[k], b);
       ent[r * 4 * na + pos] = e;
     }
   }
@@ -526,7 +546,7 @@ __device__ __forceinline__ void angular_block(int t0, int nch, int ne, int na, i
 #pragma unroll
       for (int j = 0; j < RB; ++j) {
         const int t = t0 + j * nch;
-        if (t < ne) acc[j] += (A)e.w * (A)E[t * na + e.b];
+        if (t < ne) acc[j] += (A)e.weight() * (A)E[t * na + e.b];
       }
     }
   }
@@ -555,6 +575,24 @@ __device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, in
     for (; t0 + 3 * nch < ne; t0 += 4 * nch) angular_block<4, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
     for (; t0 + nch < ne; t0 += 2 * nch) angular_block<2, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
     for (; t0 < ne; t0 += nch) angular_block<1, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
+  }
+}
+
+// Pole nodes of a Gauss-Lobatto mu grid (mu = -1 and +1): the n_ph cells of
+// such a node are one direction, so content the remap moves into the node is
+// spread evenly over them.  The angular pass deposits with linear Phi
+// weights; replacing each pole node's cells by their mean, row by row, gives
+// the even spread (the node's total is unchanged) and does not depend on Phi*,
+// which is ill-conditioned next to the pole.  X: [nrows][na]; whole block,
+// no barrier inside (the caller synchronises before and after).
+template <typename T>
+__device__ __forceinline__ void pole_mean(T* X, int nrows, int na, int nmu, int nph) {
+  for (int q = threadIdx.x; q < 2 * nrows; q += blockDim.x) {
+    T* c = X + (size_t)(q >> 1) * na + ((q & 1) ? (nmu - 1) * nph : 0);
+    T sum = T(0);
+    for (int k = 0; k < nph; ++k) sum += c[k];
+    sum = sum / T(nph);
+    for (int k = 0; k < nph; ++k) c[k] = sum;
   }
 }
 
@@ -1215,6 +1253,23 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         }
       }
       __syncthreads();
+      if (tb.pole) {
+        // pole nodes of the remapped stencil values: rows of the cells P and
+        // Q, and of the outer cell the node's flow direction reads (the same
+        // for all of a pole node's cells: they share one direction)
+        for (int q = tid; q < 6 * NE; q += NT) {
+          const int k = q / (2 * NE), side = (q / NE) & 1, t = q % NE;
+          const int j = side ? NMU - 1 : 0;
+          const int slot = k == 0 ? (S.vns[j * NPH] >= T(0) ? 0 : 3) : k;
+          if (F.z[slot] < 0 || (k == 0 && F.type != F_INTERNAL)) continue;
+          T* c = SRC + slot * nbin + t * NA + j * NPH;
+          T sum = T(0);
+          for (int kk = 0; kk < NPH; ++kk) sum += c[kk];
+          sum = sum / T(NPH);
+          for (int kk = 0; kk < NPH; ++kk) c[kk] = sum;
+        }
+        __syncthreads();
+      }
       const T* G0 = SRC;
       const T* G1 = SRC + nbin;
       const T* G2 = SRC + 2 * nbin;
@@ -1410,6 +1465,13 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   }
 
   if constexpr (MODE == 1) return;   // the face pass ends here
+  if (MODE == 0 && tb.pole) {
+    // pole nodes of the summed deposits (the even spread is linear, so one
+    // mean of the sum equals the sum of the faces' means); before the mixed
+    // path's exact-total correction, which then also covers its rounding
+    pole_mean(S.dN, NS * NE, NA, NMU, NPH);
+    __syncthreads();
+  }
   if constexpr (MODE == 2) {
     // gather this zone's deposits in the fused kernel's order: faces in
     // order; per face the rows P side then Q side, the exact totals Q side
@@ -1425,24 +1487,46 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     }
     // exact totals and outflow tallies of the zone's records
     if (warp == 0) zone_records(tb, rec, zone, a, b, nface, NS, sizeof(T) == 4, S.dtot, S.tally);
+    // all of an element's rows are loaded before they are summed in order
+    auto gather = [&](const T* base, int q) {
+      T v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < nrow) v[k] = base[(size_t)rows[k] * NS * nbin + q];
+      DN acc = DN(0);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < nrow) acc += (DN)v[k];
+      return acc;
+    };
+    if (tb.pole) {
+      // pole nodes: gather all species, spread the pole nodes' sums evenly
+      // (as the fused kernel does), then find the correction below
+      for (int s = 0; s < NS; ++s) {
+        const T* base = dep + ((size_t)zone * 6 * NS + s) * nbin;
+        DN* dNs = S.dN + (size_t)s * nbin;
+        for (int q = tid; q < nbin; q += NT) dNs[q] = gather(base, q);
+      }
+      __syncthreads();
+      pole_mean(S.dN, NS * NE, NA, NMU, NPH);
+      __syncthreads();
+    }
     for (int s = 0; s < NS; ++s) {
-      // all of an element's rows are loaded before they are summed in order;
-      // the mixed path's exact-total correction is found in the same pass
+      // the mixed path's exact-total correction is found in the gathering
+      // pass (or, with pole nodes, in a pass over the spread sums)
       const T* base = dep + ((size_t)zone * 6 * NS + s) * nbin;
       DN* dNs = S.dN + (size_t)s * nbin;
       ff part = ff{0.0f, 0.0f};
       float bk = -1.0f;
       int bi = 0x7fffffff;
       for (int q = tid; q < nbin; q += NT) {
-        T v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < nrow) v[k] = base[(size_t)rows[k] * NS * nbin + q];
-        DN acc = DN(0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < nrow) acc += (DN)v[k];
-        dNs[q] = acc;
+        DN acc;
+        if (tb.pole) {
+          acc = dNs[q];
+        } else {
+          acc = gather(base, q);
+          dNs[q] = acc;
+        }
         if (sizeof(T) == 4) {
           const float c = (float)acc * (float)S.dGam[q / NA];
           part = ff_add(part, two_prod((float)acc, (float)S.dGam[q / NA]));
@@ -1880,8 +1964,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st)
     ff partc = ff{0.0f, 0.0f};
     float bk = -1.0f;
     int bi = 0x7fffffff;
+    if (gact) angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
+    if (tb.pole) {
+      __syncthreads();
+      pole_mean(S.dst, NE, NA, NMU, NPH);
+      __syncthreads();
+    }
     if (gact) {
-      angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
       if (sizeof(T) == 4)
         for (int i = gc; i < NE; i += nch) {
           const int q = i * NA + gb;

@@ -72,6 +72,7 @@ class Problem:
     cfl: float = 0.5
     n_steps: int = 100
     alternate: bool = False      # alternate backgrounds[0]/[1] every step
+    mu_quadrature: str = "legendre"   # mu cells: "legendre" or "lobatto" (nodes at mu = +-1)
 
     @property
     def n_r(self) -> int:
@@ -240,11 +241,15 @@ def cc_background_pair(r_edges, n_theta, eps_edges, scales, seed,
 
 
 def cc2d(n_r=256, n_theta=64, n_e=12, n_mu=8, n_phi=10, scales=(1.0, 0.5, 0.2),
-         seed=None, name="cc2d", n_steps=100) -> Problem:
+         seed=None, name="cc2d", n_steps=100, opacity_scale=1.0) -> Problem:
     seed = BASE_SEED + 2 if seed is None else seed
     r_edges = np.geomspace(1e6, 1e8, n_r + 1)
     eps_edges = np.geomspace(2.0, 200.0, n_e + 1)
     bgs = cc_background_pair(r_edges, n_theta, eps_edges, list(scales), seed)
+    if opacity_scale != 1.0:
+        for bg in bgs:
+            bg.kappa_a = bg.kappa_a * opacity_scale
+            bg.kappa_s = bg.kappa_s * opacity_scale
     fe = bgs[0].f_eq
     f0 = fe[:, :, :, None] * np.ones(n_mu * n_phi)
     kinds = [NUE, NUEBAR, NUX, NUX, NUX, NUX][:len(scales)]
@@ -256,6 +261,16 @@ def config3(seed=None) -> Problem:
     """2D axisymmetric 256 r x 64 theta, 12 groups on [2, 200] MeV,
     80 angles (8 mu x 10 Phi), 3 species with opacity scales 1, 0.5, 0.2."""
     return cc2d(seed=seed, name="config3_cc2d_256x64x12x80x3")
+
+
+def config3_transport(seed=None) -> Problem:
+    """Config 3's grid, backgrounds and initial f with every opacity scaled by
+    1e-6: at the Courant step (about 1e3 cm) kappa dt is below 1 in most
+    zones and groups (it reaches 1e7 in the innermost core of config 3), so
+    the step's result is decided by the fluxes and remaps rather than reset
+    to f_eq by the collision -- the case an accuracy measure of the remap
+    and fluxes needs."""
+    return cc2d(seed=seed, name="config3_transport_cc2d_256x64x12x80x3_kappa1e-6", opacity_scale=1e-6)
 
 
 def config5_problems(seed=None) -> List[Problem]:
@@ -373,5 +388,5 @@ def random_2d(seed: int, n_r=10, n_theta=6, n_e=4, n_mu=4, n_phi=6, n_s=2,
 
 
 def by_name(name: str) -> Problem:
-    table = {"config1": config1, "config2": config2, "config3": config3}
+    table = {"config1": config1, "config2": config2, "config3": config3, "config3_transport": config3_transport}
     return table[name]()

@@ -37,7 +37,15 @@ def _cases():
         "slab": slab,
         # shifts of several energy groups (the energy pass's general rows)
         "2d_narrow_groups": narrow,
+        # Gauss-Lobatto mu cells: pole nodes spread in both passes
+        "2d_lobatto": _lob(W.random_2d(16, n_r=8, n_theta=5, n_e=4, n_mu=5, n_phi=6, n_s=2)),
+        "origin_lobatto": _lob(W.random_2d(17, n_r=6, n_theta=4, n_e=3, n_mu=6, n_phi=7, n_s=1, r_min=0.0)),
     }
+
+
+def _lob(p):
+    p.mu_quadrature = "lobatto"
+    return p
 
 
 def _run(gpu, p, precision, shape, steps, dt):
@@ -54,7 +62,8 @@ def _run(gpu, p, precision, shape, steps, dt):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", ["column", "origin", "2d", "2d_origin_ragged", "slab", "2d_narrow_groups"])
+@pytest.mark.parametrize("case", ["column", "origin", "2d", "2d_origin_ragged", "slab", "2d_narrow_groups",
+                                  "2d_lobatto", "origin_lobatto"])
 def test_split_equals_fused(gpu, case, precision):
     p = _cases()[case]
     a = _run(gpu, p, precision, 256, 6, 0.004)

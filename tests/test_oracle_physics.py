@@ -329,11 +329,11 @@ def test_spherical_diffusion_wave(orc):
 # --------------------------------------------------------------------------
 # Relativistic radiating spheres (Sec. 4.2): invariants in vacuum
 # --------------------------------------------------------------------------
-def _relativistic_sphere(nr, lapse, shock):
-    r_edges = np.geomspace(0.5, 8.0, nr + 1)
+def _relativistic_sphere(nr, lapse, shock, n_mu=8, r_max=8.0):
+    r_edges = np.geomspace(0.5, r_max, nr + 1)
     rc = 0.5 * (r_edges[1:] + r_edges[:-1])
     n_e = 12
-    p = W.homogeneous_sphere(n_r=nr, n_e=n_e, n_mu=8, n_phi=4, dang=math.log(16) / nr)
+    p = W.homogeneous_sphere(n_r=nr, n_e=n_e, n_mu=n_mu, n_phi=4, dang=math.log(r_max / 0.5) / nr)
     p.r_edges = r_edges
     p.eps_edges = np.geomspace(4.0, 240.0, n_e + 1)
     bg = p.backgrounds[0]
@@ -350,7 +350,7 @@ def _relativistic_sphere(nr, lapse, shock):
     if shock:
         vs = GOLDEN["relativistic_sphere_shock"]["v_shock"]
         bg.v[:, 0] = np.where(rc < 3.0, 0.0, np.where(rc < 3.5, vs * (rc - 3.0) / 0.5, vs * (3.5 / rc) ** 2))
-    p.f0 = np.zeros((1, nr, n_e, 32))
+    p.f0 = np.zeros((1, nr, n_e, n_mu * 4))
     return p, rc
 
 
@@ -387,3 +387,107 @@ def test_doppler_invariants(orc):
     m = (rc > 1.5) & (rc < 7.5)
     assert (eav[m].max() - eav[m].min()) / eav[m].mean() < 0.05
     assert (L[m].max() - L[m].min()) / L[m].mean() < 0.10
+
+
+# --------------------------------------------------------------------------
+# Gauss-Lobatto mu grid (Sec. 3.1; mu = 1 as a collocation point, Sec. 5)
+# --------------------------------------------------------------------------
+def _lobatto(p):
+    p.mu_quadrature = "lobatto"
+    return p
+
+
+@pytest.mark.parametrize("geom", ["column", "2d"])
+def test_lobatto_conserves_number_and_keeps_poles_even(orc, geom):
+    # moving, curved backgrounds without absorption: content + outflow is
+    # conserved.  The pole nodes (mu = +-1) are one direction each and the
+    # remap spreads what it moves into them evenly over their Phi cells, so
+    # a distribution even over a pole node's cells stays even (to the bit:
+    # the cells see the same numbers), and no mu target is ever clamped.
+    if geom == "column":
+        p = _lobatto(W.random_column(71, n_r=10, n_e=4, n_mu=6, n_phi=4, n_s=1))
+    else:
+        p = _lobatto(W.random_2d(72, n_r=7, n_theta=5, n_e=3, n_mu=5, n_phi=6, n_s=1))
+    for bg in p.backgrounds:
+        bg.kappa_a[:] = 0.0
+    f0 = p.f0.reshape(p.n_species, p.n_zone, p.n_eps, p.n_mu, p.n_phi).copy()
+    for j in (0, p.n_mu - 1):
+        f0[..., j, :] = f0[..., j, :1]
+    p.f0 = f0.reshape(p.f0.shape)
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    N0 = o.totals()[0]
+    dt = o.max_dt(0.5)
+    for k in range(8):
+        o.set_background(p.backgrounds[(k + 1) % 2])
+        o.step(dt)
+    N, _, No, _ = o.totals()
+    assert np.allclose(N + No, N0, rtol=1e-13, atol=0)
+    f = o.get_f().reshape(f0.shape)
+    for j in (0, p.n_mu - 1):
+        assert np.all(f[..., j, :] == f[..., j, :1])
+    assert o.clamp_counts()[1] == 0
+    # a Gauss-Legendre grid on the same backgrounds does clamp mu targets
+    p.mu_quadrature = "legendre"
+    o2, _ = orc.run(p, n_steps=2, dt=dt)
+    assert o2.clamp_counts()[1] > 0
+
+
+def test_lobatto_sphere_steady_state(orc):
+    # the homogeneous sphere (Sec. 4.1) on a Lobatto grid meets the paper's
+    # MSD bound as the Legendre grid does
+    tau = GOLDEN["radiating_sphere_setup"]["tau_low"]
+    p = _lobatto(W.homogeneous_sphere(n_r=24, kappa=tau, n_e=1, n_mu=16, n_phi=4, dang=0.25))
+    o = orc.Oracle(p)
+    o.set_background(p.backgrounds[0])
+    o.set_f(p.f0)
+    dt = o.max_dt(0.5)
+    for _ in range(int(6.0 / dt)):
+        o.step(dt)
+    J, H, K = o.jhk()
+    rc = 0.5 * (p.r_edges[1:] + p.r_edges[:-1])
+    m = (rc > 1.0) & (rc < 2.0)
+    ex = np.array([sphere_exact(r, ka=tau) for r in rc[m]])
+    dH = np.sqrt(np.mean((H[0, m, 0] / J[0, m, 0] - ex[:, 0]) ** 2))
+    dK = np.sqrt(np.mean((K[0, m, 0] / J[0, m, 0] - ex[:, 1]) ** 2))
+    ref = GOLDEN["radiating_sphere_msd_boltzmann"]
+    assert dH < ref["delta_H_over_J"] and dK < ref["delta_K_over_J"]
+
+
+def test_redshift_invariants_lobatto(orc):
+    # Sec. 4.2 gravitational well: in vacuum the redshift-corrected
+    # luminosity L_rs = 16 pi alpha^2 phi^4 H r^2 and alpha <eps> are constant
+    # (agreement shown graphically in the paper; tolerances are ours and
+    # reflect 32 radial zones and 16 mu cells)
+    p, rc = _relativistic_sphere(32, lapse=True, shock=False, n_mu=16)
+    _lobatto(p)
+    o, dt = _run(orc, p, 0)
+    for _ in range(int(30.0 / dt)):
+        o.step(dt)
+    L, eav = _invariants(o, p, rc)
+    m = (rc > 1.5) & (rc < 7.5)
+    assert (eav[m].max() - eav[m].min()) / eav[m].mean() < 0.01
+    assert (L[m].max() - L[m].min()) / L[m].mean() < 0.12
+
+
+@pytest.mark.slow
+def test_doppler_invariants_paper_profile(orc):
+    # Sec. 4.2 stalled-shock profile as printed: a 4 km sphere, v = 0 below
+    # 135 km, linear to -0.2c at 150 km, -0.2c (150 km/r)^2 outside.  In
+    # vacuum (1+v)/(1-v) L_rs and gamma (1+v) alpha <eps> are constant.
+    cfg = GOLDEN["relativistic_sphere_shock"]
+    R = GOLDEN["relativistic_sphere_lapse"]["sphere_radius_km"]
+    r1, r2 = cfg["r_inner_km"] / R, cfg["r_shock_km"] / R
+    p, rc = _relativistic_sphere(48, lapse=False, shock=False, n_mu=16, r_max=64.0)
+    _lobatto(p)
+    vs = cfg["v_shock"]
+    p.backgrounds[0].v[:, 0] = np.where(rc < r1, 0.0, np.where(rc < r2, vs * (rc - r1) / (r2 - r1),
+                                                                 vs * (r2 / rc) ** 2))
+    o, dt = _run(orc, p, 0)
+    for _ in range(int(80.0 / dt)):
+        o.step(dt)
+    L, eav = _invariants(o, p, rc)
+    m = (rc > 1.5) & (rc < 0.9 * 64.0)
+    assert (eav[m].max() - eav[m].min()) / eav[m].mean() < 0.01
+    assert (L[m].max() - L[m].min()) / L[m].mean() < 0.05

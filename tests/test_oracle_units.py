@@ -372,3 +372,34 @@ def test_volumes_fill_sphere_wedge(orc):
     dph = 0.02
     v = sum(orc.cell_volume(0.0, 1.0, th[b], th[b + 1], dph) for b in range(n))
     assert math.isclose(v, 2.0 / 3.0 * dph, rel_tol=1e-3)
+
+
+# --------------------------------------------------------------------------
+# Gauss-Lobatto mu grid (Sec. 3.1: cell widths are the Gauss-Lobatto weights)
+# --------------------------------------------------------------------------
+def test_gauss_lobatto_textbook(orc):
+    # closed forms of the small rules (nodes +-1 and the roots of P'_{n-1})
+    table = {
+        2: ([-1.0, 1.0], [1.0, 1.0]),
+        3: ([-1.0, 0.0, 1.0], [1 / 3, 4 / 3, 1 / 3]),
+        4: ([-1.0, -1 / math.sqrt(5), 1 / math.sqrt(5), 1.0], [1 / 6, 5 / 6, 5 / 6, 1 / 6]),
+        5: ([-1.0, -math.sqrt(3 / 7), 0.0, math.sqrt(3 / 7), 1.0], [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10]),
+    }
+    for n, (x_ref, w_ref) in table.items():
+        x, w = orc.gauss_lobatto(n)
+        assert np.allclose(x, x_ref, atol=1e-15, rtol=0)
+        assert np.allclose(w, w_ref, atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("n", [6, 9, 16, 17, 32])
+def test_gauss_lobatto_exactness(orc, n):
+    # an n-point Lobatto rule integrates polynomials of degree <= 2n - 3
+    # exactly, and no more
+    x, w = orc.gauss_lobatto(n)
+    assert x[0] == -1.0 and x[-1] == 1.0 and np.all(np.diff(x) > 0)
+    for k in range(2 * n - 2):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert math.isclose(np.dot(w, x ** k), exact, rel_tol=1e-13, abs_tol=1e-14)
+    if n <= 9:   # the degree 2n - 2 error is visible while n is small
+        k = 2 * n - 2
+        assert abs(np.dot(w, x ** k) - 2.0 / (k + 1)) > 1e-6
