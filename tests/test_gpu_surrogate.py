@@ -234,3 +234,30 @@ def test_zero_tolerance_in_the_split_form(gpu):
     assert np.array_equal(a.get_f(), b.get_f())
     n_eval, n_trip = b.sur_stats()
     assert n_eval > 0 and n_trip == n_eval
+
+
+def test_learned_remap_parity_gate(orc, gpu):
+    # A transport-dominated case (random 2D backgrounds, opacities x 0.02:
+    # kappa dt < 0.004), where errors of the remap weights are not damped by
+    # the collision.  Against the FP64 oracle after 20 steps: with a trip
+    # tolerance of 1e-4 bins the learned remap meets the mixed path's bar of
+    # 1e-4 relative L1; the error, and the share of rows that keep the
+    # network's weights, grow with the tolerance.
+    from paper_2003_02845_gb300 import workloads as W
+    p = W.random_2d(81, n_r=12, n_theta=8, n_e=6, n_mu=6, n_phi=8, n_s=2)
+    for bg in p.backgrounds:
+        bg.kappa_a *= 0.02
+        bg.kappa_s *= 0.02
+    o, dt = orc.run(p, n_steps=20)
+    fo = o.get_f()
+    s = _trained_network(gpu, p, epochs=4, n=200000, seed=61)
+    errs, used = [], []
+    for tol in (1e-4, 1e-3, 1e-2, 1e-1):
+        t = _run(gpu, p, 20, s, tol, dt)
+        f = t.get_f().astype(np.float64)
+        errs.append(np.abs(f - fo).sum() / np.abs(fo).sum())
+        n_eval, n_trip = t.sur_stats()
+        used.append(1.0 - n_trip / n_eval)
+    assert errs[0] <= 1e-4, errs
+    assert errs[0] < errs[1] < errs[2] < errs[3], errs
+    assert used[0] <= used[1] <= used[2] <= used[3] and used[3] > 0.3, used
