@@ -89,6 +89,13 @@ typedef struct bt_handle bt_handle;
  *                 point), n_mu >= 2.  The nodes mu = -1 and +1 are then one
  *                 direction each, held by n_phi cells; content the remap
  *                 moves into such a pole node is spread evenly over its cells.
+ *  theta_max      2D grids (theta_periodic == 0): the polar range is
+ *                 [0, theta_max], split uniformly into n_theta rows; 0 means
+ *                 pi.  Below pi the face at theta_max is an open boundary
+ *                 (Sec. 4.5.2, the radiating disk): bins leaving the grid
+ *                 through it are lost to the outflow tallies, and bins
+ *                 entering take the distribution set by bt_set_boundary
+ *                 (zero, i.e. vacuum, until set).
  *  precision      BT_FP64 or BT_MIXED (float32 f, fluxes and remap; float64
  *                 collision solve, content accumulators and sums).
  *  phase_norm     the 1/h^3 factor of the hydro source terms (Eq. hydrosource).
@@ -110,6 +117,7 @@ typedef struct bt_config {
   double phase_norm;
   void* stream;
   int32_t mu_quadrature;
+  double theta_max;
 } bt_config;
 
 /* Message of the last failed call on this host thread (never NULL). */
@@ -139,6 +147,15 @@ int bt_set_background(bt_handle* h, int mem,
                       const double* v, const double* alpha, const double* phi,
                       const double* shift,
                       const double* kappa_a, const double* kappa_s, const double* f_eq);
+
+/* Distribution imposed on the bins that enter the grid through the open
+ * face at theta_max (Sec. 4.5.2: an isotropic distribution imposed along the
+ * boundary theta = pi/2), isotropic in the face's comoving frame, per
+ * [s][radial zone a][group] (n_species x n_r x n_eps doubles; host or
+ * device pointer as `mem` says).  BT_ERR_ARG if the grid has no open face
+ * (theta_max == pi, a column or a slab).  It stays until set again; the
+ * flux through the face counts in the outflow tallies (negative inflow). */
+int bt_set_boundary(bt_handle* h, int mem, const double* f_boundary);
 
 /* Copy f in/out (layout above; float64 for BT_FP64, float32 for BT_MIXED).
  * bt_set_f takes f as given in the current background's comoving frames and

@@ -43,7 +43,8 @@ def lib():
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)
         L.orc_create.restype = p
-        L.orc_create.argtypes = [i, i, i, dp, i, d, d, i, ip, i, dp, i, i, d, i]
+        L.orc_create.argtypes = [i, i, i, dp, i, d, d, i, ip, i, dp, i, i, d, i, d]
+        L.orc_set_boundary.argtypes = [p, dp]
         L.orc_destroy.argtypes = [p]
         L.orc_set_background.argtypes = [p, dp, dp, dp, dp, dp, dp]
         L.orc_set_f.argtypes = [p, dp]
@@ -232,7 +233,11 @@ class Oracle:
         self.h = L.orc_create(prob.geom, prob.n_r, prob.n_theta, _dp(r_e), int(prob.theta_periodic),
                               float(prob.dtheta_column), float(prob.dphi), prob.n_species, _ip(kinds),
                               prob.n_eps, _dp(e_e), prob.n_mu, prob.n_phi, phase_norm,
-                              1 if getattr(prob, "mu_quadrature", "legendre") == "lobatto" else 0)
+                              1 if getattr(prob, "mu_quadrature", "legendre") == "lobatto" else 0,
+                              float(getattr(prob, "theta_max", 0.0) or 0.0))
+        fbc = getattr(prob, "f_boundary", None)
+        if fbc is not None:
+            self.set_boundary(fbc)
         self.shape = (prob.n_species, prob.n_zone, prob.n_eps, prob.n_ang)
 
     def close(self):
@@ -249,6 +254,12 @@ class Oracle:
     def set_background(self, bg):
         a = [_f64(bg.v), _f64(bg.alpha), _f64(bg.phi), _f64(bg.kappa_a), _f64(bg.kappa_s), _f64(bg.f_eq)]
         lib().orc_set_background(self.h, *[_dp(x) for x in a])
+
+    def set_boundary(self, fbc):
+        """Distribution imposed on the incoming bins of the open face at
+        theta_max, [species][radial zone][group]."""
+        fbc = _f64(fbc).reshape(self.prob.n_species, self.prob.n_r, self.prob.n_eps)
+        lib().orc_set_boundary(self.h, _dp(fbc))
 
     def set_f(self, f):
         f = _f64(f).reshape(self.shape)

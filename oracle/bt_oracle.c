@@ -391,6 +391,8 @@ double orc_cell_volume(double r0, double r1, double th0, double th1, double dphi
 typedef struct {
   int geom, n_r, n_th, periodic_th;
   double dth_col, dphi;
+  double th_max;               /* 2D polar range [0, th_max]; th_max < pi: open face at th_max */
+  double *fbc;                 /* [s][n_r][e] distribution imposed on the incoming bins of the th_max face */
   double *r_e, *th_e;
   int n_s, n_e, n_mu, n_ph, n_ang;
   int lobatto;                 /* [R-2] mu cells on Gauss-Lobatto nodes (pole nodes mu = +-1) */
@@ -422,8 +424,11 @@ static size_t nrow(const orc_t *o) { return (size_t)o->n_e * o->n_ang; }
  * eps_i = 3/4 (e+^4 - e-^4)/(e+^3 - e-^3);  dGamma_i = (e+^3 - e-^3)/3. */
 orc_t *orc_create(int geom, int n_r, int n_th, const double *r_edges, int periodic_th,
                   double dth_col, double dphi, int n_s, const int *kind,
-                  int n_e, const double *e_edges, int n_mu, int n_ph, double phase_norm, int lobatto) {
+                  int n_e, const double *e_edges, int n_mu, int n_ph, double phase_norm, int lobatto,
+                  double th_max) {
   orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
+  o->th_max = (th_max > 0.0 && !periodic_th && geom == ORC_SPHERICAL) ? th_max : PI_;
+  o->fbc = (double *)calloc((size_t)n_s * n_r * n_e, sizeof(double));
   o->lobatto = lobatto && n_mu >= 2;
   o->geom = geom; o->n_r = n_r; o->n_th = n_th; o->periodic_th = periodic_th;
   o->dth_col = dth_col; o->dphi = dphi; o->n_s = n_s; o->n_e = n_e;
@@ -434,7 +439,7 @@ orc_t *orc_create(int geom, int n_r, int n_th, const double *r_edges, int period
   if (periodic_th) {
     o->th_e[0] = 0.5*PI_ - 0.5*dth_col; o->th_e[1] = 0.5*PI_ + 0.5*dth_col;
   } else {
-    for (int b = 0; b <= n_th; ++b) o->th_e[b] = PI_ * b / n_th;
+    for (int b = 0; b <= n_th; ++b) o->th_e[b] = o->th_max * b / n_th;
   }
   o->kind = (int *)malloc(sizeof(int) * n_s);
   memcpy(o->kind, kind, sizeof(int) * n_s);
@@ -486,7 +491,7 @@ void orc_destroy(orc_t *o) {
   free(o->mu); free(o->dmu); free(o->Phc); free(o->dOm); free(o->vol); free(o->f);
   free(o->v); free(o->v0); free(o->al); free(o->al0); free(o->ph); free(o->ph0);
   free(o->ka); free(o->ks); free(o->fe); free(o->dN); free(o->dE); free(o->dP);
-  free(o->N_out); free(o->E_out); free(o);
+  free(o->N_out); free(o->E_out); free(o->fbc); free(o);
 }
 
 /* [R-18] a background set after another one marks a time remap for the next
@@ -509,6 +514,12 @@ void orc_set_background(orc_t *o, const double *v, const double *al, const doubl
   memcpy(o->ks, ks, sizeof(double)*NO);
   memcpy(o->fe, fe, sizeof(double)*NO);
   o->has_bg = 1;
+}
+
+/* [R-15b] distribution imposed on the incoming bins of the open face at
+ * th_max (isotropic in the face's comoving frame), [s][radial zone][group] */
+void orc_set_boundary(orc_t *o, const double *fbc) {
+  memcpy(o->fbc, fbc, sizeof(double) * (size_t)o->n_s * o->n_r * o->n_e);
 }
 
 void orc_set_f(orc_t *o, const double *f) {
@@ -635,6 +646,8 @@ typedef struct {
   double x[4];             /* 1D positions along the stencil */
   loc_t S;                 /* face frame and background */
   double xs, area;
+  int imposed;             /* open face whose incoming bins take fbc of radial zone `ra` */
+  int ra;
 } face_t;
 
 static void zone_loc(const orc_t *o, int zone, double th, double ph, loc_t *L) {
@@ -705,11 +718,18 @@ static int make_r_face(orc_t *o, int b, int a, face_t *F) {
   return 1;
 }
 
-/* Polar face of a 2D grid at edge bf (between rows bf-1 and bf), radius a. */
+/* Polar face of a 2D grid at edge bf (between rows bf-1 and bf), radius a.
+ * bf == n_th with th_max < pi: the open face at th_max (P = the last row);
+ * outgoing bins leave, incoming bins take the imposed fbc [R-15b]. */
 static int make_th_face(orc_t *o, int a, int bf, face_t *F) {
   memset(F, 0, sizeof(*F));
   F->axis = 1;
   F->type = FACE_INTERNAL;
+  if (bf == o->n_th) {
+    F->type = FACE_OUTFLOW_P;
+    F->imposed = 1;
+    F->ra = a;
+  }
   double the = o->th_e[bf], rc = r_c(o, a);
   F->area = orc_face_area_th(o->r_e[a], o->r_e[a+1], the, o->dphi);
   if (F->area == 0.0) return 0;
@@ -850,12 +870,14 @@ static void face_flux(orc_t *o, const face_t *F, int s, double dt, double *flux)
     /* [R-15] open boundary: outgoing bins take the present cell's value,
      * incoming bins see vacuum */
     int k = F->type == FACE_OUTFLOW_P ? 1 : 2;
-    for (int i = 0; i < o->n_e; ++i)
+    for (int i = 0; i < o->n_e; ++i) {
+      double fin = F->imposed ? o->fbc[((size_t)s*o->n_r + F->ra)*o->n_e + i] : 0.0;
       for (int ang = 0; ang < o->n_ang; ++ang) {
         size_t q = (size_t)i*o->n_ang + ang;
         int out = F->type == FACE_OUTFLOW_P ? (vn[ang] >= 0.0) : (vn[ang] < 0.0);
-        fs[q] = out ? g[k][q] : 0.0;
+        fs[q] = out ? g[k][q] : fin;
       }
+    }
   } else { /* FACE_REFLECT_Q: specular wall at rest [R-15] */
     for (int i = 0; i < o->n_e; ++i)
       for (int ang = 0; ang < o->n_ang; ++ang) {
@@ -947,8 +969,9 @@ static int build_faces(orc_t *o, face_t **out) {
     if (o->periodic_th) {
       for (int z = 0; z < nz(o); ++z) n += make_periodic_face(o, z, 1, &fc[n]);
     } else {
+      int last = o->th_max < PI_ ? o->n_th : o->n_th - 1;   /* the open face at th_max */
       for (int a = 0; a < o->n_r; ++a)
-        for (int bf = 1; bf < o->n_th; ++bf) n += make_th_face(o, a, bf, &fc[n]);
+        for (int bf = 1; bf <= last; ++bf) n += make_th_face(o, a, bf, &fc[n]);
     }
     for (int z = 0; z < nz(o); ++z) n += make_periodic_face(o, z, 2, &fc[n]);
   }
@@ -1249,7 +1272,7 @@ static int sur_face(orc_t *o, int zone, int fidx, face_t *F) {
       return b >= 1 ? make_th_face(o, a, b, F) : 0;
     case 3:
       if (!sph || o->periodic_th) return 0;
-      return b + 1 < o->n_th ? make_th_face(o, a, b + 1, F) : 0;
+      return (b + 1 < o->n_th || o->th_max < PI_) ? make_th_face(o, a, b + 1, F) : 0;
     case 4:
       return sph ? make_periodic_face(o, zone, 2, F) : 0;
   }

@@ -33,7 +33,7 @@ class BtConfig(C.Structure):
         ("n_eps", C.c_int32), ("eps_edges", C.POINTER(C.c_double)),
         ("n_mu", C.c_int32), ("n_phi", C.c_int32), ("precision", C.c_int32),
         ("phase_norm", C.c_double), ("stream", C.c_void_p),
-        ("mu_quadrature", C.c_int32),
+        ("mu_quadrature", C.c_int32), ("theta_max", C.c_double),
     ]
 
 
@@ -67,6 +67,7 @@ def lib():
         L.bt_destroy.argtypes = [vp]
         L.bt_set_background.argtypes = [vp, i32] + [dp] * 10
         L.bt_set_f.argtypes = [vp, i32, vp]
+        L.bt_set_boundary.argtypes = [vp, i32, vp]
         L.bt_get_f.argtypes = [vp, i32, vp]
         L.bt_max_dt.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
         L.bt_step.argtypes = [vp, C.c_double]
@@ -148,6 +149,7 @@ def make_config(prob, precision: str, stream_handle: int, phase_norm: float = 1.
     cfg.stream = stream_handle
     cfg.mu_quadrature = BT_GAUSS_LOBATTO if getattr(prob, "mu_quadrature", "legendre") == "lobatto" \
         else BT_GAUSS_LEGENDRE
+    cfg.theta_max = float(getattr(prob, "theta_max", 0.0) or 0.0)
     return cfg
 
 
@@ -185,6 +187,8 @@ class Transport:
         _check(L.bt_create(C.byref(cfg), C.c_void_p(aligned), C.byref(h)))
         self.h = h
         self.owned = True
+        if getattr(prob, "f_boundary", None) is not None:
+            self.set_boundary(prob.f_boundary)
 
     def close(self):
         if getattr(self, "h", None) and getattr(self, "owned", False):
@@ -209,6 +213,13 @@ class Transport:
         """Device (torch float64, contiguous) background."""
         _check(lib().bt_set_background(self.h, BT_MEM_DEVICE, None, None, None, _ptr(v), _ptr(alpha), _ptr(phi),
                                        None, _ptr(kappa_a), _ptr(kappa_s), _ptr(f_eq)))
+
+    def set_boundary(self, fbc):
+        """Distribution imposed on the incoming bins of the open face at
+        theta_max, [species][radial zone][group] (host numpy)."""
+        a = _host64(fbc).reshape(self.prob.n_species, self.prob.n_r, self.prob.n_eps)
+        self._keep_bc = np.ascontiguousarray(a)
+        _check(lib().bt_set_boundary(self.h, BT_MEM_HOST, _ptr(self._keep_bc)))
 
     def set_f(self, f):
         if isinstance(f, np.ndarray):

@@ -240,7 +240,7 @@ namespace {
 // Offsets of every device buffer inside one workspace.
 struct WsPlan {
   size_t tables[32];
-  size_t bg[2][3], ka, ks, fe, f[2], mom_N, mom_E, mom_P, out_N, out_E, acc, red, flag, qye, tmp;
+  size_t bg[2][3], ka, ks, fe, fbc, f[2], mom_N, mom_E, mom_P, out_N, out_E, acc, red, flag, qye, tmp;
   size_t ftab;   // float32 copies of the zone-independent tables
   size_t total;
 };
@@ -271,6 +271,7 @@ int plan(const bt_config* c, WsPlan& P, size_t* tab_sizes) {
   P.ka = L.take(8 * ns * nz * ne);
   P.ks = L.take(8 * ns * nz * ne);
   P.fe = L.take(8 * ns * nz * ne);
+  P.fbc = L.take(8 * ns * (size_t)c->n_r * ne);
   P.f[0] = L.take(fel * ns * nz * ne * nang);
   P.f[1] = L.take(fel * ns * nz * ne * nang);
   P.mom_N = L.take(8 * ns * nz);
@@ -323,6 +324,9 @@ int validate(const bt_config* c) {
   if (c->mu_quadrature != BT_GAUSS_LEGENDRE && c->mu_quadrature != BT_GAUSS_LOBATTO)
     return fail(BT_ERR_ARG, "mu_quadrature");
   if (c->mu_quadrature == BT_GAUSS_LOBATTO && c->n_mu < 2) return fail(BT_ERR_ARG, "Gauss-Lobatto needs n_mu >= 2");
+  if (!(c->theta_max >= 0.0 && c->theta_max <= kPi)) return fail(BT_ERR_ARG, "theta_max out of [0, pi]");
+  if (c->theta_max > 0.0 && c->theta_max < kPi && (c->geom != BT_GEOM_SPHERICAL || c->theta_periodic))
+    return fail(BT_ERR_ARG, "theta_max < pi needs a 2D spherical grid");
   return BT_OK;
 }
 
@@ -451,6 +455,9 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   const size_t nz = (size_t)nr * nth;
   const bool slab = c->geom == BT_GEOM_SLAB;
   const double dph = slab ? 0.0 : c->dphi_wedge;
+  // 2D polar range [0, theta_max]; below pi the face at theta_max is open
+  const bool th_open = !slab && !c->theta_periodic && c->theta_max > 0.0 && c->theta_max < kPi;
+  const double th_max = th_open ? c->theta_max : kPi;
   std::vector<double> mu, wmu;
   const bool lobatto = c->mu_quadrature == BT_GAUSS_LOBATTO;
   if (lobatto) gauss_lobatto(nmu, mu, wmu);
@@ -479,7 +486,7 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
     th_e[0] = 0.5 * kPi - 0.5 * c->dtheta_column;
     th_e[1] = 0.5 * kPi + 0.5 * c->dtheta_column;
   } else {
-    for (int b = 0; b <= nth; ++b) th_e[b] = kPi * b / nth;
+    for (int b = 0; b <= nth; ++b) th_e[b] = th_max * b / nth;
   }
   for (int b = 0; b < nth; ++b) th_c[b] = 0.5 * (th_e[b] + th_e[b + 1]);
   std::vector<double> vol(nz), ar(nth * (nr + 1)), at((nth + 1) * nr, 0.0), ap(nth * nr, 0.0);
@@ -506,7 +513,7 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
       double tht = std::atan2(std::sin(the) * cph2, std::cos(the));
       for (int k = 0; k < 4; ++k) rotation(thc + (k - 1) * d, 0.0, tht, 0.0, &Gt[9 * k]);
     } else {
-      for (int e = 1; e < nth; ++e) {
+      for (int e = 1; e < (th_open ? nth + 1 : nth); ++e) {
         for (int a = 0; a < nr; ++a) at[e * nr + a] = area_t(r_e[a], r_e[a + 1], th_e[e], dph);
         double tht = std::atan2(std::sin(th_e[e]) * cph2, std::cos(th_e[e]));
         for (int k = 0; k < 4; ++k) {
@@ -547,6 +554,7 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
 
   bt::Tables& T = h->tb;
   T.geom = c->geom; T.slab = slab; T.periodic_th = !slab && c->theta_periodic;
+  T.th_open = th_open;
   T.inner_zero = !slab && r_e[0] == 0.0; T.inner_reflect = !slab && r_e[0] > 0.0;
   T.n_r = nr; T.n_th = nth; T.n_zone = (int)nz; T.n_s = c->n_species; T.n_e = ne;
   T.n_mu = nmu; T.n_ph = nph; T.n_ang = nang;
@@ -583,6 +591,7 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   S.out_N = D(P.out_N); S.out_E = D(P.out_E); S.acc = D(P.acc); S.red = D(P.red);
   S.flag = reinterpret_cast<int*>(base + P.flag);
   S.ka = h->ka; S.ks = h->ks; S.fe = h->fe;
+  S.fbc = D(P.fbc);
   S.qye = h->qye;
   S.phase_norm = c->phase_norm;
   h->nzone = nz;
@@ -590,6 +599,7 @@ int bt_create(const bt_config* c, void* workspace, bt_handle** out) {
   h->fbytes = h->nbin_total * (h->mixed ? 4 : 8);
   cudaMemsetAsync(h->f[0], 0, h->fbytes, h->stream);
   cudaMemsetAsync(S.acc, 0, 8 * 4 * c->n_species, h->stream);
+  cudaMemsetAsync(D(P.fbc), 0, 8 * (size_t)c->n_species * nr * ne, h->stream);
   cudaMemsetAsync(S.flag, 0, 16, h->stream);
   cudaMemsetAsync(S.mom_N, 0, 8 * c->n_species * nz, h->stream);
   cudaMemsetAsync(S.mom_E, 0, 8 * c->n_species * nz, h->stream);
@@ -713,6 +723,15 @@ int bt_set_background(bt_handle* h, int mem, const double* rho, const double* T,
   h->has_bg = true;
   if (h->n_bg < 2) ++h->n_bg;
   return BT_OK;
+}
+
+int bt_set_boundary(bt_handle* h, int mem, const double* f_boundary) {
+  if (!h || !f_boundary) return fail(BT_ERR_ARG, "NULL");
+  if (mem != BT_MEM_HOST && mem != BT_MEM_DEVICE) return fail(BT_ERR_ARG, "mem");
+  if (!h->tb.th_open) return fail(BT_ERR_ARG, "the grid has no open face at theta_max");
+  const size_t n = (size_t)h->cfg.n_species * h->cfg.n_r * h->cfg.n_eps;
+  if (mem == BT_MEM_HOST && !finite_all(f_boundary, n)) return fail(BT_ERR_BACKGROUND, "non-finite boundary value");
+  return copy_in(h, mem, const_cast<double*>(h->st.fbc), f_boundary, 8 * n);
 }
 
 int bt_set_f(bt_handle* h, int mem, const void* f) {

@@ -19,6 +19,8 @@ enum Axis { AX_R = 0, AX_TH = 1, AX_PH = 2, AX_TIME = 3 };
 struct Tables {
   int geom, slab, periodic_th, inner_reflect, inner_zero;
   int n_r, n_th, n_zone, n_s, n_e, n_mu, n_ph, n_ang;
+  int th_open;         // 2D grid on [0, theta_max < pi]: the face at theta_max is open, its
+                       // incoming bins take State::fbc
   int pole;            // Gauss-Lobatto mu grid: nodes 0 and n_mu-1 are mu = -1, +1, whose
                        // n_ph cells are one direction; remapped content is spread evenly over them
   double R;            // constant ratio of consecutive group centres
@@ -38,7 +40,8 @@ struct Tables {
   const double* th_e;  // [n_th + 1]
   const double* th_c;  // [n_th]
   const double* area_r;  // [n_th][n_r + 1] radial faces
-  const double* area_t;  // [n_th + 1][n_r] polar faces (column: [1][n_r], the periodic face)
+  const double* area_t;  // [n_th + 1][n_r] polar faces (column: [1][n_r], the periodic face;
+                         // edge n_th is the open face when th_open)
   const double* area_p;  // [n_th][n_r] azimuthal (periodic) faces
   const double* G_r;     // [n_th][9]       cell triad -> radial-face triad of row b
   const double* G_t;     // [n_th + 1][4][9] stencil cell k -> polar face (column: [1][4][9])
@@ -63,6 +66,7 @@ struct State {
   const double* ka;     // [s][zone][e]
   const double* ks;
   const double* fe;
+  const double* fbc;    // [s][n_r][e] imposed on the incoming bins of the open face at theta_max
   double* mom_N;        // [s][zone]
   double* mom_E;        // [s][zone]
   double* mom_P;        // [s][zone][3]

@@ -40,6 +40,7 @@ struct Wt {
 
 struct FaceDesc {
   int type, axis, own;  // own: 1 = P, 2 = Q, 3 = both (periodic face)
+  int bc;               // open face at theta_max: incoming bins take State::fbc
   int z[4];             // zone of stencil slot k (P-1, P, Q, Q+1), -1 absent
   const double* G[4];   // rotation: slot k triad -> face triad (row-major 3x3)
   double x[4], xs, dx, area;
@@ -605,6 +606,7 @@ __device__ __forceinline__ void pole_mean(T* X, int nrows, int na, int nmu, int 
 __device__ bool make_face(const Tables& tb, const State& st, int a, int b, int fidx, FaceDesc& F) {
   const int nr = tb.n_r;
   const int zone = b * nr + a;
+  F.bc = 0;
   for (int k = 0; k < 4; ++k) { F.z[k] = -1; F.G[k] = nullptr; F.x[k] = 0.0; }
   const double* Gr = tb.slab ? nullptr : tb.G_r + 9 * b;
   if (fidx == 0 || fidx == 1) {
@@ -634,9 +636,10 @@ __device__ bool make_face(const Tables& tb, const State& st, int a, int b, int f
       F.xs = rc * (thc + 0.5 * d);
     } else {
       int edge = fidx == 2 ? b : b + 1;
-      if (edge == 0 || edge == tb.n_th) return false;
+      if (edge == 0 || (edge == tb.n_th && !tb.th_open)) return false;
       F.area = tb.area_t[edge * nr + a];
       F.own = fidx == 2 ? 2 : 1;
+      if (edge == tb.n_th) { F.type = F_OUTFLOW_P; F.bc = 1; }   // the open face at theta_max
       for (int k = 0; k < 4; ++k) {
         int bb = edge - 2 + k;
         if (bb >= 0 && bb < tb.n_th) { F.z[k] = bb * nr + a; F.G[k] = tb.G_t + 9 * (4 * edge + k); F.x[k] = rc * tb.th_c[bb]; }
@@ -960,7 +963,7 @@ __device__ __forceinline__ bool face_exists(const Tables& tb, int a, int b, int 
   if (fidx == 2 || fidx == 3) {
     if (tb.periodic_th) return fidx == 2 && tb.area_t[a] != 0.0;
     const int edge = fidx == 2 ? b : b + 1;
-    if (edge == 0 || edge == tb.n_th) return false;
+    if (edge == 0 || (edge == tb.n_th && !tb.th_open)) return false;
     return tb.area_t[edge * nr + a] != 0.0;
   }
   return tb.area_p[b * nr + a] != 0.0;
@@ -1368,7 +1371,9 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
             }
             fs = (T(1) - w) * flw + w * fu;
           } else if (F.type == F_OUTFLOW_P) {
-            fs = up ? G1[q] : T(0);
+            // incoming bins: vacuum, or the distribution imposed on the open
+            // face at theta_max [R-15b]
+            fs = up ? G1[q] : (F.bc ? (T)st.fbc[((size_t)s * tb.n_r + a) * NE + i] : T(0));
           } else if (F.type == F_OUTFLOW_Q) {
             fs = vn < T(0) ? G2[q] : T(0);
           } else {  // reflecting wall at rest

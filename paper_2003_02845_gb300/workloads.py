@@ -73,6 +73,8 @@ class Problem:
     n_steps: int = 100
     alternate: bool = False      # alternate backgrounds[0]/[1] every step
     mu_quadrature: str = "legendre"   # mu cells: "legendre" or "lobatto" (nodes at mu = +-1)
+    theta_max: float = 0.0       # 2D polar range [0, theta_max] (0: pi); below pi the face at theta_max is open
+    f_boundary: Optional[np.ndarray] = None   # [n_s, n_r, n_e] imposed on that face's incoming bins
 
     @property
     def n_r(self) -> int:
@@ -385,6 +387,46 @@ def random_2d(seed: int, n_r=10, n_theta=6, n_e=4, n_mu=4, n_phi=6, n_s=2,
     kinds = [NUE, NUEBAR, NUX, NUX, NUX, NUX][:n_s]
     return Problem(name, GEOM_SPHERICAL, r_edges, n_theta, False, 0.0, dphi, kinds, eps_edges,
                    n_mu, n_phi, bgs, f0, 0.5, 10, True)
+
+
+def radiating_disk(n_r=40, n_theta=16, n_mu=8, n_phi=8, r_min=0.05, r_max=3.0, disk_radius=1.0, dphi=0.3,
+                   quadrature="lobatto") -> Problem:
+    """The radiating disk of Sec. 4.5.2: vacuum everywhere on 0 < theta < pi/2,
+    and an isotropic f = 1 imposed on the incoming bins of the theta = pi/2
+    face for the radial zones whose centre lies inside disk_radius (an
+    optically thick, geometrically thin disk).  r log-spaced from r_min
+    (a reflecting wall) to r_max; one group; f = 0 initially."""
+    r_edges = np.geomspace(r_min, r_max, n_r + 1)
+    rc = 0.5 * (r_edges[:-1] + r_edges[1:])
+    bg = _flat_background(n_r * n_theta, 1, 1)
+    fbc = np.zeros((1, n_r, 1))
+    fbc[0, rc < disk_radius, 0] = 1.0
+    f0 = np.zeros((1, n_r * n_theta, 1, n_mu * n_phi))
+    p = Problem("radiating_disk", GEOM_SPHERICAL, r_edges, n_theta, False, 0.0, dphi, [NUE],
+                np.array([1.0, 2.0]), n_mu, n_phi, [bg], f0, 0.5, 0)
+    p.theta_max = 0.5 * np.pi
+    p.f_boundary = fbc
+    p.mu_quadrature = quadrature
+    return p
+
+
+def radiating_sphere_2d(n_r=24, n_theta=8, n_mu=12, n_phi=8, tau=4.0, r_min=0.2, r_max=2.0, dphi=0.3,
+                        quadrature="lobatto") -> Problem:
+    """The homogeneous radiating sphere (Sec. 4.1) on the 2D grid (Sec. 4.5.1):
+    kappa_a = tau inside r < 1, vacuum outside, f_eq = 1, f = 0 initially;
+    r log-spaced from r_min (a reflecting wall deep inside the sphere) to
+    r_max, theta on [0, pi]."""
+    r_edges = np.geomspace(r_min, r_max, n_r + 1)
+    rc = 0.5 * (r_edges[:-1] + r_edges[1:])
+    nz = n_r * n_theta
+    bg = _flat_background(nz, 1, 1)
+    bg.kappa_a[0, np.tile(rc, n_theta) < 1.0, 0] = tau
+    bg.f_eq[0, :, 0] = 1.0
+    f0 = np.zeros((1, nz, 1, n_mu * n_phi))
+    p = Problem("radiating_sphere_2d", GEOM_SPHERICAL, r_edges, n_theta, False, 0.0, dphi, [NUE],
+                np.array([1.0, 2.0]), n_mu, n_phi, [bg], f0, 0.5, 0)
+    p.mu_quadrature = quadrature
+    return p
 
 
 def by_name(name: str) -> Problem:

@@ -388,3 +388,45 @@ def test_launch_shapes_cover_every_angle(orc, gpu):
     t.set_f(p.f0)
     assert t.autotune(0.01) & 0xffff >= 192
     o, t2, dt = compare_run(orc, gpu, p, 4)
+
+
+# ---------------------------------------------------------------------------
+# Axisymmetric tests of Sec. 4.5 at oracle sizes: the 2D radiating sphere and
+# the radiating disk's open face at theta = pi/2 (imposed inflow)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
+def test_radiating_sphere_2d_parity(orc, gpu, precision, tol):
+    p = W.radiating_sphere_2d(n_r=10, n_theta=6, n_mu=6, n_phi=6)
+    compare_run(orc, gpu, p, 40, precision=precision, tol=tol)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
+@pytest.mark.parametrize("shape", [256, 0x10000 | 256])
+def test_radiating_disk_parity(orc, gpu, precision, tol, shape):
+    p = W.radiating_disk(n_r=10, n_theta=5, n_mu=6, n_phi=6, r_min=0.2, r_max=2.0)
+    o, dt = orc.run(p, n_steps=30)
+    t = gpu.Transport(p, precision)
+    t.set_launch_shape(shape)
+    t.set_background(p.backgrounds[0])
+    t.set_f(p.f0)
+    assert math.isclose(t.max_dt(0.5), dt, rel_tol=1e-12)
+    for _ in range(30):
+        t.step(dt)
+    fo = o.get_f()
+    assert rel_l1(t.get_f(), fo) <= tol
+    No, Ng = o.totals(), t.totals()
+    for a, b in zip(Ng, No):
+        assert np.allclose(a, b, rtol=1e-12 if precision == "fp64" else 1e-5, atol=0)
+
+
+def test_open_face_needs_a_2d_grid(gpu):
+    p = W.random_column(91, n_r=4, n_e=2, n_mu=2, n_phi=2, n_s=1)
+    t = gpu.Transport(p, "fp64")
+    with pytest.raises(gpu.BtError) as e:
+        t.set_boundary(np.zeros((1, 4, 2)))
+    assert e.value.code == -1
+    q = W.random_column(92, n_r=4, n_e=2, n_mu=2, n_phi=2, n_s=1)
+    q.theta_max = 1.0
+    with pytest.raises(gpu.BtError) as e:
+        gpu.Transport(q, "fp64")
+    assert e.value.code == -1
