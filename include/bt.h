@@ -176,6 +176,35 @@ int bt_max_dt(bt_handle* h, double cfl, double* dt_out);
  * bt_totals, bt_sur_stats, bt_autotune). */
 int bt_step(bt_handle* h, double dt);
 
+/* Local time stepping (Sec. 5: the global step is limited by the small
+ * zones at the centre, while larger outer zones could take larger steps).
+ * Zone z advances with its own step dt0 2^levels[z], levels in [0, n_levels);
+ * bt_step_lts(h, dt0) advances every zone by the macro step dt0 2^(n_levels-1):
+ *   - the time remap (if a background was set) runs once, first;
+ *   - at substep k (of dt0) every face whose finer side has level l is
+ *     evaluated if k is a multiple of 2^l, over dt0 2^l, from the current f
+ *     (a coarser neighbour's f is still that of the start of its step); its
+ *     flux goes to both sides and waits there until the side's step ends, so
+ *     number is conserved face by face (Eq. fullstep);
+ *   - a zone whose step ends at substep k ((k + 1) a multiple of 2^level)
+ *     then takes its collision solve over its own step (Sec. 3.5);
+ *   - bt_moments then returns the source terms averaged over the macro step,
+ *     and the outflow tallies cover the macro step.
+ * It uses the split flux form (split/256 if the handle's shape is fused; the
+ * deposit rows are allocated as for bt_set_launch_shape) and updates f in
+ * place.  It does not run with a learned remap (BT_ERR_ARG).
+ * bt_set_levels installs levels (host array [zone], 1 <= n_levels <= 16).
+ * bt_lts_levels computes them from the current background: dt0 = cfl / (the
+ * largest per-zone Courant rate, as bt_max_dt), each zone the largest level
+ * l < max_levels with dt0 2^l within its own limit cfl / rate, then lowered
+ * until radial (and, on 2D grids, polar) neighbours differ by at most one
+ * level; it installs them, returns dt0 and, if `levels` is not NULL, the
+ * levels (host [zone]).  bt_n_levels returns the installed number. */
+int bt_set_levels(bt_handle* h, const int32_t* levels, int n_levels);
+int bt_lts_levels(bt_handle* h, double cfl, int max_levels, double* dt0, int32_t* levels);
+int bt_n_levels(const bt_handle* h);
+int bt_step_lts(bt_handle* h, double dt0);
+
 /* Collision source terms of the last step (Eq. hydrosource), per unit
  * coordinate volume and time: dN[s][zone], dE[s][zone] (comoving energy),
  * dP[s][zone][3] (comoving momentum, local triad), Q_Ye[zone] =

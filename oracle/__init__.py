@@ -53,6 +53,11 @@ def lib():
         L.orc_step_zones.argtypes = [p, d, ip, dp]
         L.orc_max_dt.restype = d
         L.orc_max_dt.argtypes = [p, d]
+        L.orc_zone_rates.argtypes = [p, dp]
+        L.orc_lts_levels.restype = d
+        L.orc_lts_levels.argtypes = [p, d, i, ip]
+        L.orc_step_lts.restype = i
+        L.orc_step_lts.argtypes = [p, d, ip, i]
         L.orc_moments.argtypes = [p, dp, dp, dp, dp]
         L.orc_totals.argtypes = [p, dp, dp, dp, dp]
         L.orc_jhk.argtypes = [p, dp, dp, dp]
@@ -282,6 +287,25 @@ class Oracle:
 
     def max_dt(self, cfl: float) -> float:
         return lib().orc_max_dt(self.h, float(cfl))
+
+    def zone_rates(self) -> np.ndarray:
+        """Per-zone Courant rate (max over bins of the outflow rate)."""
+        out = np.zeros(self.prob.n_zone)
+        lib().orc_zone_rates(self.h, _dp(out))
+        return out
+
+    def lts_levels(self, cfl: float, max_levels: int):
+        """(dt0, levels [zone]) of the local time stepping (reading R-19)."""
+        lev = np.zeros(self.prob.n_zone, dtype=np.int32)
+        dt0 = lib().orc_lts_levels(self.h, float(cfl), int(max_levels), _ip(lev))
+        return dt0, lev
+
+    def step_lts(self, dt0: float, levels, n_levels: int):
+        """One local-time-stepping macro step of dt0 2^(n_levels-1): zone z
+        steps with dt0 2^levels[z]."""
+        lev = np.ascontiguousarray(np.asarray(levels, dtype=np.int32))
+        if lib().orc_step_lts(self.h, float(dt0), _ip(lev), int(n_levels)) != 0:
+            raise ValueError("levels out of range")
 
     def moments(self):
         S, Z = self.prob.n_species, self.prob.n_zone

@@ -988,18 +988,16 @@ static int build_faces(orc_t *o, face_t **out) {
 /* ------------------------------------------------------------------------- */
 enum { FACE_BLOCK = 256 };   /* faces whose deposits are computed together */
 
-static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
+/* Fluxes of the faces q with dtf[q] > 0 (each over its own dtf[q]) from the
+ * current f, deposited into both neighbours' content changes dN (Eq.
+ * fullstep), outflow added to the tallies. */
+static void deposit_faces(orc_t *o, const face_t *faces, int nf, const double *dtf, double *dN) {
   int Z = nz(o);
   size_t R = nrow(o);
-  if (o->remap_pending) { time_remap(o); o->remap_pending = 0; }
-  face_t *faces;
-  int nf = build_faces(o, &faces);
-  double *dN = (double *)calloc((size_t)o->n_s * Z * R, sizeof(double));
   double *flux = (double *)malloc(sizeof(double) * R * FACE_BLOCK);
   double *depP = (double *)malloc(sizeof(double) * R * FACE_BLOCK);
   double *depQ = (double *)malloc(sizeof(double) * R * FACE_BLOCK);
   double tally[2 * FACE_BLOCK];
-  int act[FACE_BLOCK];
   for (int s = 0; s < o->n_s; ++s)
     for (int q0 = 0; q0 < nf; q0 += FACE_BLOCK) {
       int nb = nf - q0 < FACE_BLOCK ? nf - q0 : FACE_BLOCK;
@@ -1009,17 +1007,13 @@ static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
 #endif
       for (int k = 0; k < nb; ++k) {
         const face_t *F = &faces[q0 + k];
-        act[k] = 1;
-        if (sel) {  /* subset mode: only faces that touch a selected zone */
-          int zp = F->z[1], zq = F->z[2];
-          if (!((zp >= 0 && sel[zp]) || (zq >= 0 && sel[zq]))) { act[k] = 0; continue; }
-        }
-        face_flux(o, F, s, dt, flux + (size_t)k * R);
+        if (!(dtf[q0 + k] > 0.0)) continue;
+        face_flux(o, F, s, dtf[q0 + k], flux + (size_t)k * R);
         face_deposit(o, F, flux + (size_t)k * R, depP + (size_t)k * R, depQ + (size_t)k * R, tally + 2 * k);
       }
       /* added to the zones in face-list order */
       for (int k = 0; k < nb; ++k) {
-        if (!act[k]) continue;
+        if (!(dtf[q0 + k] > 0.0)) continue;
         const face_t *F = &faces[q0 + k];
         for (int side = 1; side <= 2; ++side) {
           if (F->z[side] < 0) continue;
@@ -1034,6 +1028,17 @@ static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
       }
     }
   free(flux); free(depP); free(depQ);
+}
+
+/* Collision of the zones with dtz[z] > 0 (Sec. 3.5) over their own dtz[z]:
+ * f* = f + dN / (phi^6 dV u^0 dGamma dOmega), the implicit solve, f^{n+1}
+ * into dst (o->f, or `out` in subset mode); the zone's dN rows are then
+ * spent (zeroed).  Moments (Eq. hydrosource): the content change over dtz
+ * per unit volume, per unit of `tm` (the time the moments average over):
+ * written (acc = 0) or added (acc = 1). */
+static void collide_zones(orc_t *o, const double *dtz, double *dN, double *out, double tm, int acc) {
+  int Z = nz(o);
+  size_t R = nrow(o);
 #ifdef _OPENMP
 #pragma omp parallel
 #endif
@@ -1048,7 +1053,8 @@ static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
 #pragma omp for schedule(dynamic, 4)
 #endif
     for (int z = 0; z < Z; ++z) {
-      if (sel && !sel[z]) continue;
+      double dt = dtz[z];
+      if (!(dt > 0.0)) continue;
       loc_t X;
       zone_loc(o, z, 0.0, 0.0, &X);
       for (int ang = 0; ang < o->n_ang; ++ang) {
@@ -1064,33 +1070,140 @@ static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
           double ka = o->ka[zo], ks = o->ks[zo], fe = o->fe[zo];
           size_t base = ((size_t)s*Z + z)*R + (size_t)i*o->n_ang;
           const double *f = o->f + base;
-          const double *dn = dN + base;
+          double *dn = dN + base;
           for (int ang = 0; ang < o->n_ang; ++ang) {
             fst[ang] = f[ang] + dn[ang] / (c6 * o->vol[z] * u0[ang] * o->dGam[i] * o->dOm[ang]);
             r[ang] = fst[ang] + tau[ang]*ka*fe;
+            dn[ang] = 0.0;
           }
           orc_collision_row(o->n_ang, r, tau, ka, ks, o->dOm, fnew);
-          double *dst = sel ? out + base : o->f + base;
+          double *dst = out ? out + base : o->f + base;
           for (int ang = 0; ang < o->n_ang; ++ang) {
             /* collision moments (Eq. hydrosource) [R-17]: content change per
              * coordinate volume and time */
-            double dc = c6 * u0[ang] * o->dGam[i] * o->dOm[ang] * (fnew[ang] - fst[ang]) / dt;
+            double dc = c6 * u0[ang] * o->dGam[i] * o->dOm[ang] * (fnew[ang] - fst[ang]) / tm;
             sN += dc;
             sE += dc * o->e_c[i];
             for (int m = 0; m < 3; ++m) sP[m] += dc * o->e_c[i] * nd[3*ang+m];
             dst[ang] = fnew[ang];
           }
         }
-        o->dN[(size_t)s*Z + z] = sN;
-        o->dE[(size_t)s*Z + z] = sE;
-        for (int m = 0; m < 3; ++m) o->dP[((size_t)s*Z + z)*3 + m] = sP[m];
+        size_t q = (size_t)s*Z + z;
+        if (acc) {
+          o->dN[q] += sN; o->dE[q] += sE;
+          for (int m = 0; m < 3; ++m) o->dP[q*3 + m] += sP[m];
+        } else {
+          o->dN[q] = sN; o->dE[q] = sE;
+          for (int m = 0; m < 3; ++m) o->dP[q*3 + m] = sP[m];
+        }
       }
     }
     free(r); free(tau); free(fst); free(fnew); free(u0); free(nd);
   }
-  free(dN); free(faces);
 }
 
+static void step_impl(orc_t *o, double dt, const int *sel, double *out) {
+  int Z = nz(o);
+  size_t R = nrow(o);
+  if (o->remap_pending) { time_remap(o); o->remap_pending = 0; }
+  face_t *faces;
+  int nf = build_faces(o, &faces);
+  double *dN = (double *)calloc((size_t)o->n_s * Z * R, sizeof(double));
+  double *dtf = (double *)malloc(sizeof(double) * (nf > 0 ? nf : 1));
+  double *dtz = (double *)malloc(sizeof(double) * Z);
+  for (int q = 0; q < nf; ++q) {
+    dtf[q] = dt;
+    if (sel) {  /* subset mode: only faces that touch a selected zone */
+      int zp = faces[q].z[1], zq = faces[q].z[2];
+      if (!((zp >= 0 && sel[zp]) || (zq >= 0 && sel[zq]))) dtf[q] = 0.0;
+    }
+  }
+  for (int z = 0; z < Z; ++z) dtz[z] = (sel && !sel[z]) ? 0.0 : dt;
+  deposit_faces(o, faces, nf, dtf, dN);
+  collide_zones(o, dtz, dN, sel ? out : NULL, dt, 0);
+  free(dN); free(faces); free(dtf); free(dtz);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Local time stepping (Sec. 5: "the timestep can be much larger in the      */
+/* larger outer zones") [R-19]: zone z advances with dt0 2^lev[z], lev in     */
+/* [0, L); one call advances every zone by the macro step dt0 2^(L-1).  At   */
+/* substep k (of dt0) a face whose finer side has level l = min(lev_P,      */
+/* lev_Q) is evaluated when k is a multiple of 2^l, over dt0 2^l, from the   */
+/* current f (a coarser neighbour's f is still that of the start of its own */
+/* step); its deposit goes to both sides, where it waits until the side's   */
+/* step ends (Eq. fullstep; number conserved face by face).  A zone whose    */
+/* step ends at substep k, (k + 1) a multiple of 2^lev, then takes its        */
+/* collision over its own step (Sec. 3.5).  Moments are averaged over the   */
+/* macro step.  The time remap runs once, before the first substep.         */
+/* ------------------------------------------------------------------------- */
+int orc_step_lts(orc_t *o, double dt0, const int *lev, int L) {
+  int Z = nz(o);
+  size_t R = nrow(o);
+  if (L < 1 || L > 16) return -1;
+  for (int z = 0; z < Z; ++z) if (lev[z] < 0 || lev[z] >= L) return -1;
+  if (o->remap_pending) { time_remap(o); o->remap_pending = 0; }
+  face_t *faces;
+  int nf = build_faces(o, &faces);
+  double *dN = (double *)calloc((size_t)o->n_s * Z * R, sizeof(double));
+  double *dtf = (double *)malloc(sizeof(double) * (nf > 0 ? nf : 1));
+  double *dtz = (double *)malloc(sizeof(double) * Z);
+  const int K = 1 << (L - 1);
+  const double tm = dt0 * K;
+  for (size_t q = 0; q < (size_t)o->n_s * Z; ++q) o->dN[q] = o->dE[q] = 0.0;
+  for (size_t q = 0; q < (size_t)o->n_s * Z * 3; ++q) o->dP[q] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    for (int q = 0; q < nf; ++q) {
+      int zp = faces[q].z[1], zq = faces[q].z[2];
+      int l = zp >= 0 ? lev[zp] : lev[zq];
+      if (zp >= 0 && zq >= 0 && lev[zq] < l) l = lev[zq];
+      dtf[q] = (k % (1 << l)) == 0 ? dt0 * (1 << l) : 0.0;
+    }
+    for (int z = 0; z < Z; ++z) dtz[z] = ((k + 1) % (1 << lev[z])) == 0 ? dt0 * (1 << lev[z]) : 0.0;
+    deposit_faces(o, faces, nf, dtf, dN);
+    collide_zones(o, dtz, dN, NULL, tm, 1);
+  }
+  free(dN); free(faces); free(dtf); free(dtz);
+  return 0;
+}
+
+/* [R-19] Levels of the local time stepping: dt0 = cfl / max rate; zone z
+ * takes the largest l < max_levels whose step dt0 2^l stays within its own
+ * limit cfl / rate[z]; then levels are lowered until zones that share a
+ * radial face (or, on 2D grids, a polar face) differ by at most one level.
+ * Returns dt0 and writes lev[zone]. */
+void orc_zone_rates(orc_t *o, double *zr);
+double orc_lts_levels(orc_t *o, double cfl, int max_levels, int *lev) {
+  int Z = nz(o);
+  double *zr = (double *)malloc(sizeof(double) * Z);
+  orc_zone_rates(o, zr);
+  double mx = 0.0;
+  for (int z = 0; z < Z; ++z) if (zr[z] > mx) mx = zr[z];
+  for (int z = 0; z < Z; ++z) {
+    int l = 0;
+    /* dt0 2^(l+1) <= cfl / rate  <=>  rate 2^(l+1) <= mx */
+    while (l + 1 < max_levels && zr[z] * (double)(1 << (l + 1)) <= mx) ++l;
+    lev[z] = l;
+  }
+  int polar = o->geom == ORC_SPHERICAL && !o->periodic_th && o->n_th > 1;
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int z = 0; z < Z; ++z) {
+      int a = z % o->n_r, b = z / o->n_r, l = lev[z];
+      if (a > 0 && lev[z - 1] + 1 < l) l = lev[z - 1] + 1;
+      if (a + 1 < o->n_r && lev[z + 1] + 1 < l) l = lev[z + 1] + 1;
+      if (polar && b > 0 && lev[z - o->n_r] + 1 < l) l = lev[z - o->n_r] + 1;
+      if (polar && b + 1 < o->n_th && lev[z + o->n_r] + 1 < l) l = lev[z + o->n_r] + 1;
+      if (l != lev[z]) { lev[z] = l; changed = 1; }
+    }
+  }
+  free(zr);
+  return cfl / mx;
+}
+
+/* Per-zone Courant rate (the quantity orc_max_dt maximises) [R-14]: rate[z]
+ * = max over bins of sum over faces of max(0, u.n_out) dA / dV. */
 int orc_step(orc_t *o, double dt) {
   step_impl(o, dt, NULL, NULL);
   return 0;
@@ -1112,7 +1225,7 @@ int orc_step_zones(orc_t *o, double dt, const int *sel, double *out) {
  * content in one step: dt <= CFL / max_{zone,bin} sum_faces max(0, u.n_out)
  * dA / dV, with u the coordinate velocity of the zone's bin expressed in the
  * face triad.  Zero-area faces do not count. */
-double orc_max_dt(orc_t *o, double cfl) {
+void orc_zone_rates(orc_t *o, double *zr) {
   face_t *faces;
   int nf = build_faces(o, &faces);
   int Z = nz(o);
@@ -1136,9 +1249,25 @@ double orc_max_dt(orc_t *o, double cfl) {
       }
     }
   }
-  double mx = 0.0;
-  for (size_t q = 0; q < (size_t)Z*o->n_ang; ++q) if (rate[q] > mx) mx = rate[q];
+  for (int z = 0; z < Z; ++z) {
+    double mx = 0.0;
+    for (int ang = 0; ang < o->n_ang; ++ang) if (rate[(size_t)z*o->n_ang + ang] > mx) mx = rate[(size_t)z*o->n_ang + ang];
+    zr[z] = mx;
+  }
   free(rate); free(faces);
+}
+
+/* [R-14] Courant limit: no bin of any zone may lose more than CFL of its
+ * content in one step: dt <= CFL / max_{zone,bin} sum_faces max(0, u.n_out)
+ * dA / dV, with u the coordinate velocity of the zone's bin expressed in the
+ * face triad.  Zero-area faces do not count. */
+double orc_max_dt(orc_t *o, double cfl) {
+  int Z = nz(o);
+  double *zr = (double *)malloc(sizeof(double) * Z);
+  orc_zone_rates(o, zr);
+  double mx = 0.0;
+  for (int z = 0; z < Z; ++z) if (zr[z] > mx) mx = zr[z];
+  free(zr);
   return cfl / mx;
 }
 

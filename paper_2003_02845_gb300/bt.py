@@ -68,6 +68,10 @@ def lib():
         L.bt_set_background.argtypes = [vp, i32] + [dp] * 10
         L.bt_set_f.argtypes = [vp, i32, vp]
         L.bt_set_boundary.argtypes = [vp, i32, vp]
+        L.bt_set_levels.argtypes = [vp, vp, i32]
+        L.bt_lts_levels.argtypes = [vp, C.c_double, i32, C.POINTER(C.c_double), vp]
+        L.bt_n_levels.argtypes = [vp]
+        L.bt_step_lts.argtypes = [vp, C.c_double]
         L.bt_get_f.argtypes = [vp, i32, vp]
         L.bt_max_dt.argtypes = [vp, C.c_double, C.POINTER(C.c_double)]
         L.bt_step.argtypes = [vp, C.c_double]
@@ -237,6 +241,25 @@ class Transport:
 
     def step(self, dt: float):
         _check(lib().bt_step(self.h, float(dt)))
+
+    # -- local time stepping ------------------------------------------------
+    def lts_levels(self, cfl: float, max_levels: int):
+        """Levels from the current background (bt_lts_levels): (dt0, levels)."""
+        dt0 = C.c_double()
+        lev = np.zeros(self.prob.n_zone, dtype=np.int32)
+        _check(lib().bt_lts_levels(self.h, float(cfl), int(max_levels), C.byref(dt0), lev.ctypes.data))
+        return dt0.value, lev
+
+    def set_levels(self, levels, n_levels: int):
+        lev = np.ascontiguousarray(np.asarray(levels, dtype=np.int32))
+        _check(lib().bt_set_levels(self.h, lev.ctypes.data, int(n_levels)))
+
+    @property
+    def n_levels(self) -> int:
+        return int(lib().bt_n_levels(self.h))
+
+    def step_lts(self, dt0: float):
+        _check(lib().bt_step_lts(self.h, float(dt0)))
 
     # -- outputs ------------------------------------------------------------
     def get_f(self, out=None) -> np.ndarray:

@@ -214,6 +214,13 @@ struct bt_handle {
   // whenever one of them is allocated, freed or swapped, so that a batch
   // graph captured with the old buffers is never replayed
   uint64_t gen = 0;
+  // local time stepping: levels [zone], the zones ordered by the level of
+  // their face pass (the finest level among their owned faces) and by their
+  // own level ([2][zone], device), and the prefix counts per level
+  int* lev_d = nullptr;
+  int* lists_d = nullptr;
+  int lts_L = 0;
+  std::vector<int> cnt_face, cnt_zone;
   // learned remap (bt_set_surrogate)
   bt_surrogate* sur = nullptr;
   void* sur_tab = nullptr;                    // [zone][31][n_ang] weights
@@ -678,6 +685,8 @@ int bt_destroy(bt_handle* h) {
   if (h->sur_counts) cudaFree(h->sur_counts);
   if (h->dep) cudaFree(h->dep);
   if (h->rec) cudaFree(h->rec);
+  if (h->lev_d) cudaFree(h->lev_d);
+  if (h->lists_d) cudaFree(h->lists_d);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;
   return BT_OK;
@@ -831,6 +840,163 @@ int bt_step(bt_handle* h, double dt) {
   if (!h->has_bg) return fail(BT_ERR_STATE, "bt_step before bt_set_background");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BT_ERR_DT, "dt must be positive and finite");
   return step_enqueue(h, dt);
+}
+
+// ---------------------------------------------------------------------------
+// Local time stepping (Sec. 5): zone z steps with dt0 2^lev[z]
+// ---------------------------------------------------------------------------
+int bt_set_levels(bt_handle* h, const int32_t* levels, int n_levels) {
+  if (!h || !levels) return fail(BT_ERR_ARG, "NULL");
+  if (n_levels < 1 || n_levels > 16) return fail(BT_ERR_ARG, "n_levels out of [1, 16]");
+  const int nr = h->cfg.n_r, nth = h->cfg.n_theta, nz = (int)h->nzone;
+  for (int z = 0; z < nz; ++z)
+    if (levels[z] < 0 || levels[z] >= n_levels) return fail(BT_ERR_ARG, "level out of [0, n_levels)");
+  const bool polar = h->cfg.geom == BT_GEOM_SPHERICAL && !h->cfg.theta_periodic && nth > 1;
+  // the face pass of a zone runs when any face it owns is due: its outer
+  // radial face and (2D) upper polar face reach the next zone; the others
+  // are its own
+  std::vector<int> lmin(nz);
+  for (int z = 0; z < nz; ++z) {
+    const int a = z % nr, b = z / nr;
+    int l = levels[z];
+    if (a + 1 < nr) l = std::min(l, (int)levels[z + 1]);
+    if (polar && b + 1 < nth) l = std::min(l, (int)levels[z + nr]);
+    lmin[z] = l;
+  }
+  std::vector<int> lists(2 * (size_t)nz);
+  h->cnt_face.assign(n_levels, 0);
+  h->cnt_zone.assign(n_levels, 0);
+  for (int z = 0; z < nz; ++z) { ++h->cnt_face[lmin[z]]; ++h->cnt_zone[levels[z]]; }
+  for (int l = 1; l < n_levels; ++l) { h->cnt_face[l] += h->cnt_face[l - 1]; h->cnt_zone[l] += h->cnt_zone[l - 1]; }
+  {
+    std::vector<int> pf(n_levels, 0), pz(n_levels, 0);
+    for (int l = 1; l < n_levels; ++l) { pf[l] = h->cnt_face[l - 1]; pz[l] = h->cnt_zone[l - 1]; }
+    for (int z = 0; z < nz; ++z) {   // stable: zones keep their order within a level
+      lists[pf[lmin[z]]++] = z;
+      lists[nz + pz[levels[z]]++] = z;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && !h->lev_d) e = cudaMalloc(&h->lev_d, sizeof(int) * nz);
+  if (e == cudaSuccess && !h->lists_d) e = cudaMalloc(&h->lists_d, sizeof(int) * 2 * (size_t)nz);
+  if (e == cudaSuccess) e = cudaMemcpy(h->lev_d, levels, sizeof(int) * nz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->lists_d, lists.data(), sizeof(int) * 2 * (size_t)nz, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "bt_set_levels");
+  h->lts_L = n_levels;
+  return BT_OK;
+}
+
+int bt_lts_levels(bt_handle* h, double cfl, int max_levels, double* dt0, int32_t* levels) {
+  if (!h || !dt0) return fail(BT_ERR_ARG, "NULL");
+  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_lts_levels before bt_set_background");
+  if (max_levels < 1 || max_levels > 16) return fail(BT_ERR_ARG, "max_levels out of [1, 16]");
+  const int nr = h->cfg.n_r, nth = h->cfg.n_theta, nz = (int)h->nzone;
+  bind_state(h);
+  double* zr = nullptr;
+  cudaError_t ce = cudaMallocAsync(reinterpret_cast<void**>(&zr), sizeof(double) * nz, h->stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "bt_lts_levels");
+  int e = bt::launch_max_rate(h->tb, h->st, h->tmp, h->stream, zr);
+  h->launches += 1;
+  std::vector<double> rate(nz);
+  double mx = 0.0;
+  if (!e) ce = cudaMemcpyAsync(rate.data(), zr, sizeof(double) * nz, cudaMemcpyDeviceToHost, h->stream);
+  if (!e && ce == cudaSuccess) ce = cudaMemcpyAsync(&mx, h->tmp, 8, cudaMemcpyDeviceToHost, h->stream);
+  cudaFreeAsync(zr, h->stream);
+  if (!e && ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail((cudaError_t)e, "zone rates");
+  if (ce != cudaSuccess) return cuda_fail(ce, "bt_lts_levels");
+  if (!(mx > 0.0)) return fail(BT_ERR_STATE, "zero transport rate");
+  // the finest step is the global Courant step; a zone takes the largest
+  // dt0 2^l within its own limit cfl / rate
+  std::vector<int32_t> lev(nz);
+  for (int z = 0; z < nz; ++z) {
+    int l = 0;
+    while (l + 1 < max_levels && rate[z] * (double)(1 << (l + 1)) <= mx) ++l;
+    lev[z] = l;
+  }
+  // neighbours (radial, and polar on 2D grids) differ by one level at most
+  const bool polar = h->cfg.geom == BT_GEOM_SPHERICAL && !h->cfg.theta_periodic && nth > 1;
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int z = 0; z < nz; ++z) {
+      const int a = z % nr, b = z / nr;
+      int l = lev[z];
+      if (a > 0) l = std::min(l, lev[z - 1] + 1);
+      if (a + 1 < nr) l = std::min(l, lev[z + 1] + 1);
+      if (polar && b > 0) l = std::min(l, lev[z - nr] + 1);
+      if (polar && b + 1 < nth) l = std::min(l, lev[z + nr] + 1);
+      if (l != lev[z]) { lev[z] = l; changed = true; }
+    }
+  }
+  int top = 0;
+  for (int z = 0; z < nz; ++z) top = std::max(top, (int)lev[z]);
+  int rc = bt_set_levels(h, lev.data(), top + 1);
+  if (rc != BT_OK) return rc;
+  *dt0 = cfl / mx;
+  if (levels) std::copy(lev.begin(), lev.end(), levels);
+  return BT_OK;
+}
+
+int bt_n_levels(const bt_handle* h) { return h ? h->lts_L : 0; }
+
+int bt_step_lts(bt_handle* h, double dt0) {
+  if (!h) return fail(BT_ERR_ARG, "NULL");
+  if (!h->has_bg) return fail(BT_ERR_STATE, "bt_step_lts before bt_set_background");
+  if (!h->lev_d) return fail(BT_ERR_STATE, "bt_step_lts before bt_set_levels / bt_lts_levels");
+  if (h->sur) return fail(BT_ERR_ARG, "the learned remap does not run with local time stepping");
+  if (!(dt0 > 0.0) || !std::isfinite(dt0)) return fail(BT_ERR_DT, "dt0 must be positive and finite");
+  const int S = bt::kShapeSplit;
+  const int nt = (h->nt & S) ? h->nt : (S | 256);   // the split form computes each face once
+  if (!shape_fits(h, nt)) return fail(BT_ERR_ARG, "the split form does not fit this problem");
+  int rc = ensure_split(h);
+  if (rc != BT_OK) return rc;
+  bind_state(h);
+  int e;
+  if (h->remap_pending) {
+    e = bt::launch_time_remap(h->tb, h->st, h->mixed, h->stream);
+    h->launches += 1;
+    if (e) return cuda_fail((cudaError_t)e, "time remap");
+    h->remap_pending = false;
+  }
+  // zones step at different times: f is updated in place (a zone pass writes
+  // only its own zones, after the face pass that read them)
+  bt::State st = h->st;
+  st.f_next = st.f;
+  const size_t nsz = (size_t)h->cfg.n_species * h->nzone;
+  cudaMemsetAsync(st.mom_N, 0, 8 * nsz, h->stream);
+  cudaMemsetAsync(st.mom_E, 0, 8 * nsz, h->stream);
+  cudaMemsetAsync(st.mom_P, 0, 8 * 3 * nsz, h->stream);
+  cudaMemsetAsync(st.out_N, 0, 8 * nsz, h->stream);
+  cudaMemsetAsync(st.out_E, 0, 8 * nsz, h->stream);
+  cudaMemsetAsync(h->qye, 0, 8 * h->nzone, h->stream);
+  st.lev = h->lev_d;
+  st.dt0 = dt0;
+  st.lts_L = h->lts_L;
+  const int L = h->lts_L, K = 1 << (L - 1);
+  for (int k = 0; k < K; ++k) {
+    st.lts_k = k;
+    // a level-l face or zone starts a step at multiples of 2^l, ends one
+    // before the next multiple: the due ones form a prefix of the lists
+    int lf = L - 1, lz = 0;
+    if (k > 0) { lf = 0; while (lf < L - 1 && (k % (1 << (lf + 1))) == 0) ++lf; }
+    while (lz < L - 1 && ((k + 1) % (1 << (lz + 1))) == 0) ++lz;
+    st.zlist = h->lists_d;
+    st.n_zlist = h->cnt_face[lf];
+    e = bt::launch_flux_collide(h->tb, st, dt0, h->mixed, nt, h->dep, h->rec, h->stream);
+    h->launches += 1;
+    if (e) return cuda_fail((cudaError_t)e, "face pass (local time stepping)");
+    st.zlist = h->lists_d + h->nzone;
+    st.n_zlist = h->cnt_zone[lz];
+    e = bt::launch_zone_collide(h->tb, st, dt0, h->mixed, h->dep, h->rec, h->stream);
+    h->launches += 1;
+    if (e) return cuda_fail((cudaError_t)e, "zone pass (local time stepping)");
+  }
+  st.zlist = nullptr;
+  st.lev = nullptr;
+  e = bt::launch_accumulate_outflow(h->tb, st, h->stream);
+  h->launches += 2;
+  if (e) return cuda_fail((cudaError_t)e, "outflow");
+  return BT_OK;
 }
 
 int bt_autotune(bt_handle* h, double dt, int* chosen_nt) {

@@ -80,6 +80,15 @@ struct State {
   // learned remap: per (zone, remap kind, source angle) weights of the
   // float32 path (nullptr: the exact weights are computed in the kernels)
   const void* sur_tab;
+  // local time stepping (split flux form): lev [zone] levels (nullptr: one
+  // global step), lts_k the substep of the macro step, dt0 the finest step,
+  // lts_L the number of levels.  zlist: the zones one flux launch handles,
+  // CTA i -> zone zlist[i] (nullptr: CTA i -> zone i).
+  const int* lev;
+  const int* zlist;
+  int n_zlist;          // zones in zlist (the flux launches' grid)
+  int lts_k, lts_L;
+  double dt0;
 };
 
 struct LaunchCfg {
@@ -104,7 +113,9 @@ size_t split_dep_bytes(const Tables& T, int mixed);
 size_t split_rec_bytes(const Tables& T);
 int launch_totals(const Tables& T, const State& S, int mixed, double* d_out /*[2*n_s]*/, void* stream);
 int launch_accumulate_outflow(const Tables& T, const State& S, void* stream);
-int launch_max_rate(const Tables& T, const State& S, double* d_rate /*[1]*/, void* stream);
+// d_zone_rates [zone] (optional): each zone's rate, whose maximum is d_rate
+int launch_max_rate(const Tables& T, const State& S, double* d_rate /*[1]*/, void* stream,
+                    double* d_zone_rates = nullptr);
 int launch_jhk(const Tables& T, const State& S, int mixed, double* J, double* H, double* K, void* stream);
 int launch_check_finite(const Tables& T, const State& S, int mixed, void* stream);
 // learned remap: features X [n][16], exact targets Y [n][27] and validity of

@@ -41,6 +41,7 @@ struct Wt {
 struct FaceDesc {
   int type, axis, own;  // own: 1 = P, 2 = Q, 3 = both (periodic face)
   int bc;               // open face at theta_max: incoming bins take State::fbc
+  int addP, addQ;       // local time stepping: add to the side's deposit row (its step began earlier)
   int z[4];             // zone of stencil slot k (P-1, P, Q, Q+1), -1 absent
   const double* G[4];   // rotation: slot k triad -> face triad (row-major 3x3)
   double x[4], xs, dx, area;
@@ -698,6 +699,7 @@ __device__ __forceinline__ double pow6(double x) {
 // Face constants in the arithmetic type (staged once per face).
 template <typename T>
 struct FaceT {
+  T dt;                     // the face's step (the step of its finer side under local time stepping)
   T xs, dx, area, al, cf, c6;
   T sP, sQ;                 // xs - x1, xs - x2
   T rdx, rdl0, rdl1, rdl2;  // reciprocals of dx and the stencil spacings
@@ -943,9 +945,12 @@ struct DepRec {
 };
 
 template <typename T>
-struct StoreDep {   // dep = sign * T[F]
-  T* dst; int na, b; T sign;
-  __device__ void operator()(int t, T acc) const { dst[t * na + b] = sign * acc; }
+struct StoreDep {   // dep = sign * T[F], or dep += sign * T[F] (a step that began earlier)
+  T* dst; int na, b; T sign; bool add;
+  __device__ void operator()(int t, T acc) const {
+    T* d = dst + t * na + b;
+    *d = add ? *d + sign * acc : sign * acc;
+  }
 };
 
 // a zone's faces owned by it in the face pass (each face has one owner)
@@ -1014,8 +1019,11 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   using DN = typename DNT<T>::type;
   FluxSmem<T> S;
   flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, MODE, &S, smem_raw);
-  const int zone = blockIdx.x;
+  const int zone = st.zlist ? st.zlist[blockIdx.x] : (int)blockIdx.x;
   const int a = zone % tb.n_r, b = zone / tb.n_r;
+  // local time stepping: the zone pass takes the zone's own step
+  const bool lts = st.lev != nullptr;
+  if (lts && MODE == 2) dt = st.dt0 * (double)(1 << st.lev[zone]);
   const int NE = tb.n_e, NA = tb.n_ang, NS = tb.n_s, NPH = tb.n_ph, NMU = tb.n_mu;
   const int nbin = NE * NA;
   const int tid = threadIdx.x;
@@ -1064,10 +1072,25 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   const int nface = tb.slab ? 2 : kFaces;
   if (MODE != 2 && tid < nface) {
     FaceDesc& Fd = S.F[tid];
+    int lf = 0;   // local time stepping: the face's level (its finer side's)
+    bool active = true;
     if ((MODE == 1 && !face_owned(tb, a, tid)) || !make_face(tb, st, a, b, tid, Fd)) {
+      active = false;
+    } else if (lts) {
+      lf = Fd.z[1] >= 0 ? st.lev[Fd.z[1]] : st.lev[Fd.z[2]];
+      if (Fd.z[1] >= 0 && Fd.z[2] >= 0) lf = min(lf, st.lev[Fd.z[2]]);
+      active = (st.lts_k % (1 << lf)) == 0;   // evaluated when its finer side starts a step
+      // a side whose own step began at an earlier substep adds to its row
+      Fd.addP = Fd.z[1] >= 0 && (st.lts_k % (1 << st.lev[Fd.z[1]])) != 0;
+      Fd.addQ = Fd.z[2] >= 0 && (st.lts_k % (1 << st.lev[Fd.z[2]])) != 0;
+    } else {
+      Fd.addP = Fd.addQ = 0;
+    }
+    if (!active) {
       Fd.type = -1;
     } else {
       FaceT<T>& ft = S.FT[tid];
+      ft.dt = lts ? (T)(st.dt0 * (double)(1 << lf)) : dtT;
       ft.xs = (T)Fd.xs; ft.dx = (T)Fd.dx; ft.area = (T)Fd.area;
       ft.al = (T)Fd.al; ft.cf = (T)Fd.cf; ft.c6 = (T)pow6(Fd.cf);
       ft.sP = (T)(Fd.xs - Fd.x[1]); ft.sQ = (T)(Fd.xs - Fd.x[2]);
@@ -1168,8 +1191,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         T vn = Ls.al / (Ls.cf * Ls.cf) * p[F.axis] / e;
         S.vns[ang] = vn;
         S.cs[ang] = T(1) / (ft.c6 * e * S.dOm[ang]);
-        S.taus[ang] = T(0.5) * dtT * ft.al / e;
-        S.vdx[ang] = T(0.5) * dtT * vn * ft.rdx;
+        S.taus[ang] = T(0.5) * ft.dt * ft.al / e;
+        S.vdx[ang] = T(0.5) * ft.dt * vn * ft.rdx;
       }
     }
     __syncthreads();
@@ -1346,7 +1369,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       const bool outflow = F.type == F_OUTFLOW_P || F.type == F_OUTFLOW_Q;
       if (gact) {
         const T vn = S.vns[gb];
-        const T fang = dtT * ft.area * ft.c6 * S.u0s[gb] * vn * S.dOm[gb];
+        const T fang = ft.dt * ft.area * ft.c6 * S.u0s[gb] * vn * S.dOm[gb];
         const int jj = gb / NPH, kk = gb % NPH;
         const int gm = (NMU - 1 - jj) * NPH + kk;   // mirror angle (reflecting wall)
         const bool up = vn >= T(0);
@@ -1427,13 +1450,22 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         const ff zero = ff{0.0f, 0.0f};
         if (depP) {
           DepRec& r = rec[((size_t)F.z[1] * 6 + 2 * F.axis + 1) * NS + s];
-          r.sum = sizeof(T) == 4 ? ff_neg(sumF) : zero;
-          r.tn = tn_sum; r.te = te_sum * F.al;
+          const ff sv = sizeof(T) == 4 ? ff_neg(sumF) : zero;
+          if (F.addP) {
+            r.sum = ff_add(r.sum, sv); r.tn += tn_sum; r.te += te_sum * F.al;
+          } else {
+            r.sum = sv; r.tn = tn_sum; r.te = te_sum * F.al;
+          }
         }
         if (depQ) {
           DepRec& r = rec[((size_t)F.z[2] * 6 + 2 * F.axis) * NS + s];
-          r.sum = sizeof(T) == 4 ? sumF : zero;
-          r.tn = depP ? 0.0 : tn_sum; r.te = depP ? 0.0 : te_sum * F.al;
+          const ff sv = sizeof(T) == 4 ? sumF : zero;
+          const double tnv = depP ? 0.0 : tn_sum, tev = depP ? 0.0 : te_sum * F.al;
+          if (F.addQ) {
+            r.sum = ff_add(r.sum, sv); r.tn += tnv; r.te += tev;
+          } else {
+            r.sum = sv; r.tn = tnv; r.te = tev;
+          }
         }
       }
       // deposits into this zone: dN -= T_{s->P}[F] (own P), dN += T_{s->Q}[F] (own Q)
@@ -1461,7 +1493,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
                                AddDN<T>{S.dN + (size_t)s * nbin, NA, gb, sgn});
           } else {
             T* d = dep + (((size_t)F.z[1 + side] * 6 + 2 * F.axis + (side == 0 ? 1 : 0)) * NS + s) * nbin;
-            angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn});
+            angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn, side == 0 ? F.addP != 0 : F.addQ != 0});
           }
         }
       }
@@ -1802,13 +1834,25 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         for (int c = 0; c < 5; ++c) acc[c] = ff_add(acc[c], zf[((size_t)s * NE + i) * 5 + c]);
       for (int c = 0; c < 5; ++c) m[c] = ff_to_d(acc[c]);
     }
-    S.corr[s] = m[0];   // the species' number source (the correction is spent)
     size_t o = (size_t)s * tb.n_zone + zone;
-    st.mom_N[o] = m[0];
-    st.mom_E[o] = m[1];
-    st.mom_P[3 * o] = m[2]; st.mom_P[3 * o + 1] = m[3]; st.mom_P[3 * o + 2] = m[4];
-    st.out_N[o] = S.tally[2 * s];
-    st.out_E[o] = S.tally[2 * s + 1];
+    if (lts) {
+      // local time stepping: the zone's steps add up to the macro step's
+      // moments (averaged over the macro step) and outflow
+      const double sc = dt / (st.dt0 * (double)(1 << (st.lts_L - 1)));
+      for (int c = 0; c < 5; ++c) m[c] *= sc;
+      st.mom_N[o] += m[0];
+      st.mom_E[o] += m[1];
+      st.mom_P[3 * o] += m[2]; st.mom_P[3 * o + 1] += m[3]; st.mom_P[3 * o + 2] += m[4];
+      st.out_N[o] += S.tally[2 * s];
+      st.out_E[o] += S.tally[2 * s + 1];
+    } else {
+      st.mom_N[o] = m[0];
+      st.mom_E[o] = m[1];
+      st.mom_P[3 * o] = m[2]; st.mom_P[3 * o + 1] = m[3]; st.mom_P[3 * o + 2] = m[4];
+      st.out_N[o] = S.tally[2 * s];
+      st.out_E[o] = S.tally[2 * s + 1];
+    }
+    S.corr[s] = m[0];   // the species' number source (the correction is spent)
   }
   __syncthreads();
   if (tid == 0) {
@@ -1820,7 +1864,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       const double m = S.corr[s];
       q += kind == 0 ? -m : m;
     }
-    st.qye[zone] = q * st.phase_norm;
+    if (lts) st.qye[zone] += q * st.phase_norm;
+    else st.qye[zone] = q * st.phase_norm;
   }
 }
 
@@ -2104,7 +2149,7 @@ __global__ void k_pack_outflow(Tables tb, State st) {
 
 // Courant rate (C-14 reading): max over zones and bins of sum over the zone's
 // faces of max(0, outward coordinate velocity) dA/dV.
-__global__ void __launch_bounds__(kThreads) k_max_rate(Tables tb, State st, unsigned long long* out) {
+__global__ void __launch_bounds__(kThreads) k_max_rate(Tables tb, State st, unsigned long long* out, double* zr) {
   __shared__ FaceDesc F;
   __shared__ double rate[kMaxAng];
   __shared__ double red[kWarps];
@@ -2146,6 +2191,7 @@ __global__ void __launch_bounds__(kThreads) k_max_rate(Tables tb, State st, unsi
     double mm = 0.0;
     for (int w = 0; w < kWarps; ++w) mm = fmax(mm, red[w]);
     atomicMax(out, (unsigned long long)__double_as_longlong(mm));
+    if (zr) zr[zone] = mm;   // per-zone rate (levels of the local time stepping)
   }
 }
 
@@ -2490,13 +2536,17 @@ int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) 
 template <typename T, int NT>
 int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void* rec, cudaStream_t s) {
   size_t sm1 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 1, nullptr, nullptr);
-  k_flux_faces<T, NT><<<tb.n_zone, NT, sm1, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
+  const int grid = st.zlist ? st.n_zlist : tb.n_zone;
+  if (grid <= 0) return 0;
+  k_flux_faces<T, NT><<<grid, NT, sm1, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
   return (int)cudaGetLastError();
 }
 template <typename T>
 int launch_zone_t(const Tables& tb, const State& st, double dt, void* dep, void* rec, cudaStream_t s) {
   size_t sm2 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 256 / 32, 2, nullptr, nullptr);
-  k_zone_collide<T><<<tb.n_zone, 256, sm2, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
+  const int grid = st.zlist ? st.n_zlist : tb.n_zone;
+  if (grid <= 0) return 0;
+  k_zone_collide<T><<<grid, 256, sm2, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
   return (int)cudaGetLastError();
 }
 
@@ -2635,10 +2685,10 @@ int launch_accumulate_outflow(const Tables& tb, const State& st, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int launch_max_rate(const Tables& tb, const State& st, double* d_rate, void* stream) {
+int launch_max_rate(const Tables& tb, const State& st, double* d_rate, void* stream, double* d_zone_rates) {
   cudaStream_t s = (cudaStream_t)stream;
   cudaMemsetAsync(d_rate, 0, sizeof(double), s);
-  k_max_rate<<<tb.n_zone, kThreads, 0, s>>>(tb, st, reinterpret_cast<unsigned long long*>(d_rate));
+  k_max_rate<<<tb.n_zone, kThreads, 0, s>>>(tb, st, reinterpret_cast<unsigned long long*>(d_rate), d_zone_rates);
   return (int)cudaGetLastError();
 }
 
