@@ -1892,9 +1892,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_zone_collide(Ta
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RemapSmem {
-  T* src; T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3;
+  T* src[2];   // species rows (bulk copies; converted in place to content per dGamma), double-buffered
+  T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3;
   Wt<T>* W; AEnt<T>* ent; short* off; unsigned* msk;
   ff* redf; float* rkey; int* ridx;
+  unsigned long long* bar;   // [2] mbarriers of the two row buffers
+  Loc<T>* L;                 // [2] the old and the new background of the zone
+  T* c6;                     // [2] their phi^6
 };
 
 template <typename T>
@@ -1906,7 +1910,9 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
     if (s) s->ptr = reinterpret_cast<type*>(base + o);         \
     o += sizeof(type) * (size_t)(count);                       \
   } while (0)
-  BT_TAKE(src, T, (size_t)ne * nang);
+  BT_TAKE(bar, unsigned long long, 2);
+  BT_TAKE(src[0], T, (size_t)ne * nang);
+  BT_TAKE(src[1], T, (size_t)ne * nang);
   BT_TAKE(E, T, (size_t)ne * nang);
   BT_TAKE(dst, T, (size_t)ne * nang);
   BT_TAKE(mu, T, nmu);
@@ -1923,48 +1929,106 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(redf, ff, 4 * kWarps);     // [species parity][input, output total][warp]
   BT_TAKE(rkey, float, 2 * kWarps);  // [species parity][warp]
   BT_TAKE(ridx, int, 2 * kWarps);
+  BT_TAKE(L, Loc<T>, 2);
+  BT_TAKE(c6, T, 2);
 #undef BT_TAKE
   return (o + 15) & ~size_t(15);
 }
 
+// The mixed path's exact-total correction of one species of a zone, by one
+// warp: the input and output content totals and the largest output bin from
+// the nw warps' partials (a shuffle tree); lane 0 rewrites that bin's f with
+// the correction, so the zone's content after the remap equals the content
+// before it exactly (float gathers round).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st) {
+__device__ void remap_correct(const Tables& tb, int nw, const ff* pin, const float* pk, const int* pi, const T* dst,
+                              T* fz, const Loc<T>& Y, T c6y, const T* n0, const T* n1, const T* n2, const T* dOm) {
+  const int lane = threadIdx.x & 31;
+  ff tot_in = lane < nw ? pin[lane] : ff{0.0f, 0.0f};
+  ff tot = lane < nw ? pin[kWarps + lane] : ff{0.0f, 0.0f};
+  float kb = lane < nw ? pk[lane] : -2.0f;
+  int at = lane < nw ? pi[lane] : 0x7fffffff;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot_in = ff_add(tot_in, ff_shfl_down(tot_in, o));
+    tot = ff_add(tot, ff_shfl_down(tot, o));
+    const float k2 = __shfl_down_sync(0xffffffffu, kb, o);
+    const int i2 = __shfl_down_sync(0xffffffffu, at, o);
+    if (k2 > kb || (k2 == kb && i2 < at)) { kb = k2; at = i2; }
+  }
+  if (lane != 0 || at < 0 || at >= tb.n_e * tb.n_ang) return;
+  const int NA = tb.n_ang, b = at % NA;
+  const double corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
+  const T u0 = Y.g * (T(1) + (Y.v[0] * n0[b] + Y.v[1] * n1[b] + Y.v[2] * n2[b]));
+  const T rc = T(1) / (c6y * u0 * dOm[b]);
+  fz[at] = (T)((double)dst[at] + corr_y) * rc;
+}
+
+// Time remap T_{n->n+1} of every zone (Sec. 3.2): old frames -> new frames,
+// one CTA per zone, the species one after another.  The species' rows come
+// by bulk asynchronous copies (the first while the weights and lists are
+// built, the next while the current species is remapped).  Two block
+// barriers per species: the energy pass reads other threads' rows of its
+// column, the angular pass other columns.  The mixed path's exact-total
+// correction of a species is made by one thread after the next barrier
+// (every thread writes its bins first, uncorrected).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) k_time_remap(Tables tb, State st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RemapSmem<T> S;
   remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, &S, smem_raw);
+  constexpr int NW = NT / 32;
   const int zone = blockIdx.x;
-  const int NE = tb.n_e, NA = tb.n_ang, NPH = tb.n_ph, NMU = tb.n_mu;
+  const int NE = tb.n_e, NA = tb.n_ang, NPH = tb.n_ph, NMU = tb.n_mu, NS = tb.n_s;
   const int nbin = NE * NA;
   const int tid = threadIdx.x;
-  const int nch = kThreads / NA > 0 ? kThreads / NA : 1;
+  const int nch = NT / NA > 0 ? NT / NA : 1;
   const int gb = tid % NA, gc = tid / NA;
   const bool gact = tid < nch * NA;
+  T* f = reinterpret_cast<T*>(st.f);
+  const unsigned rowbytes = (unsigned)(sizeof(T) * (size_t)nbin);
+  const bool use_tma = (rowbytes % 16u) == 0u;
+  auto row = [&](int s) { return f + ((size_t)s * tb.n_zone + zone) * nbin; };
+  // the first species' row, copied while the tables, weights and lists are built
+  if (tid == 0) {
+    mbar_init(S.bar, 1);
+    mbar_init(S.bar + 1, 1);
+    if (use_tma) {
+      mbar_expect_tx(S.bar, rowbytes);
+      tma_load_1d(S.src[0], row(0), rowbytes, S.bar);
+    }
+  } else if (tid == 32) {
+    // the zone's old and new frames, once (float64 loads and conversions
+    // by every thread would queue on the narrow float64 pipe)
+    make_loc(S.L[0], st.v_old + 3 * zone, st.al_old[zone], st.cf_old[zone]);
+    make_loc(S.L[1], st.v + 3 * zone, st.al[zone], st.cf[zone]);
+    S.c6[0] = (T)pow6(st.cf_old[zone]);
+    S.c6[1] = (T)pow6(st.cf[zone]);
+  }
   if constexpr (sizeof(T) == 4) {
-    for (int q = tid; q < NMU; q += kThreads) S.mu[q] = tb.f_mu[q];
-    for (int q = tid; q < NA; q += kThreads) {
+    for (int q = tid; q < NMU; q += NT) S.mu[q] = tb.f_mu[q];
+    for (int q = tid; q < NA; q += NT) {
       S.n0[q] = tb.f_n0[q]; S.n1[q] = tb.f_n1[q]; S.n2[q] = tb.f_n2[q]; S.dOm[q] = tb.f_dOm[q];
     }
-    for (int q = tid; q < NE; q += kThreads) S.dGam[q] = tb.f_dGam[q];
-    for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = tb.f_p3[q];
+    for (int q = tid; q < NE; q += NT) S.dGam[q] = tb.f_dGam[q];
+    for (int q = tid; q < 2 * NE + 3; q += NT) S.p3[q] = tb.f_p3[q];
   } else {
-    for (int q = tid; q < NMU; q += kThreads) S.mu[q] = (T)tb.mu[q];
-    for (int q = tid; q < NA; q += kThreads) {
+    for (int q = tid; q < NMU; q += NT) S.mu[q] = (T)tb.mu[q];
+    for (int q = tid; q < NA; q += NT) {
       int j = q / NPH, k = q % NPH;
       S.n0[q] = (T)tb.mu[j];
       S.n1[q] = (T)(tb.smu[j] * tb.cph[k]);
       S.n2[q] = (T)(tb.smu[j] * tb.sph[k]);
       S.dOm[q] = (T)tb.dOm[q];
     }
-    for (int q = tid; q < NE; q += kThreads) S.dGam[q] = (T)tb.dGam[q];
-    for (int q = tid; q < 2 * NE + 3; q += kThreads) S.p3[q] = (T)tb.p3[q];
+    for (int q = tid; q < NE; q += NT) S.dGam[q] = (T)tb.dGam[q];
+    for (int q = tid; q < 2 * NE + 3; q += NT) S.p3[q] = (T)tb.p3[q];
   }
   __syncthreads();
   const T* P3 = S.p3 + NE + 1;
-  Loc<T> X, Y;
-  make_loc(X, st.v_old + 3 * zone, st.al_old[zone], st.cf_old[zone]);
-  make_loc(Y, st.v + 3 * zone, st.al[zone], st.cf[zone]);
+  const Loc<T> X = S.L[0], Y = S.L[1];
   const EBr<T> Rg = make_ebr<T>((T)tb.R);
-  for (int ang = tid; ang < NA; ang += kThreads) {
+  for (int ang = tid; ang < NA; ang += NT) {
     if (sizeof(T) == 4 && st.sur_tab)
       S.W[ang] = reinterpret_cast<const Wt<T>*>(st.sur_tab)[(size_t)zone * kSurKindsAll * NA + ang];
     else
@@ -1974,30 +2038,51 @@ __global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st)
   const int em = gact ? S.W[gb].m : 0;
   const T ew = gact ? S.W[gb].we : T(0);
   build_alists(S.W, 1, 1u, NA, NMU, NPH, S.off, S.msk, S.ent);
-  const T c6x = (T)pow6(st.cf_old[zone]), c6y = (T)pow6(st.cf[zone]);
-  T* f = reinterpret_cast<T*>(st.f);
+  const T c6x = S.c6[0], c6y = S.c6[1];
+  // this thread's column: density factor of the old frame, reciprocal of the new one's
+  T cangX = T(0), rcY = T(1);
+  if (gact) {
+    const T u0x = X.g * (T(1) + (X.v[0] * S.n0[gb] + X.v[1] * S.n1[gb] + X.v[2] * S.n2[gb]));
+    const T u0y = Y.g * (T(1) + (Y.v[0] * S.n0[gb] + Y.v[1] * S.n1[gb] + Y.v[2] * S.n2[gb]));
+    cangX = c6x * u0x * S.dOm[gb];
+    rcY = T(1) / (c6y * u0y * S.dOm[gb]);
+  }
   const int lane = tid & 31, warp = tid >> 5;
-  // Per species three block barriers (two in FP64): the energy pass reads its
-  // column's rows of other threads, the angular pass other columns; every
-  // thread's angular rows are its own bins, so the correction's partials
-  // need no barrier before them, and every thread combines the warps'
-  // partials itself (no barrier after).  The partials alternate between two
-  // buffers by species parity: a thread that starts the next species cannot
-  // overwrite what a slower one still combines.
-  for (int s = 0; s < tb.n_s; ++s) {
-    T* fz = f + ((size_t)s * tb.n_zone + zone) * nbin;
+  unsigned ph0 = 0u, ph1 = 0u;   // parity of the next phase of each buffer's mbarrier
+  for (int s = 0; s < NS; ++s) {
+    T* fz = row(s);
+    const bool odd = (s & 1) != 0;
+    T* src = odd ? S.src[1] : S.src[0];
     ff* pin = S.redf + (s & 1) * 2 * kWarps;      // [0, kWarps): input total, then output total
     float* pk = S.rkey + (s & 1) * kWarps;
     int* pi = S.ridx + (s & 1) * kWarps;
-    // content per unit dGamma of the old frame: y = phi^6 u0 dOmega f
+    if (use_tma) {
+      // the next species' row into the other buffer (free since the last
+      // species' energy pass, two barriers ago)
+      unsigned long long* bar_cur = S.bar + (odd ? 1 : 0);
+      unsigned long long* bar_nxt = S.bar + (odd ? 0 : 1);
+      if (tid == 0 && s + 1 < NS) {
+        fence_proxy_async();
+        mbar_expect_tx(bar_nxt, rowbytes);
+        tma_load_1d(odd ? S.src[0] : S.src[1], row(s + 1), rowbytes, bar_nxt);
+      }
+      bool ok = mbar_wait(bar_cur, odd ? ph1 : ph0, st.flag);
+      if (odd) ph1 ^= 1u; else ph0 ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        // give a copy still in flight a bounded chance to land, then stop
+        if (tid == 0 && s + 1 < NS) mbar_wait(bar_nxt, odd ? ph0 : ph1, st.flag);
+        __syncthreads();
+        return;
+      }
+    }
+    // content per unit dGamma of the old frame, y = phi^6 u0 dOmega f, in
+    // place; the mixed path's input total
     ff part = ff{0.0f, 0.0f};
     if (gact) {
-      const T u0 = X.g * (T(1) + (X.v[0] * S.n0[gb] + X.v[1] * S.n1[gb] + X.v[2] * S.n2[gb]));
-      const T cang = c6x * u0 * S.dOm[gb];
       for (int i = gc; i < NE; i += nch) {
         const int q = i * NA + gb;
-        T d = cang * fz[q];
-        S.src[q] = d;
+        const T d = cangX * (use_tma ? src[q] : fz[q]);
+        src[q] = d;
         if (sizeof(T) == 4) part = ff_add(part, two_prod((float)d, (float)S.dGam[i]));
       }
     }
@@ -2007,32 +2092,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st)
       if (lane == 0) pin[warp] = part;
     }
     __syncthreads();
-    if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, S.src, S.E, T(1), P3);
+    // the last species' exact-total correction (its bins were all written
+    // before the barrier), by one thread while the others go on
+    if (sizeof(T) == 4 && s > 0 && warp == 0) {
+      const int sp = s - 1;
+      remap_correct<T>(tb, NW, S.redf + (sp & 1) * 2 * kWarps, S.rkey + (sp & 1) * kWarps, S.ridx + (sp & 1) * kWarps,
+                       S.dst, row(sp), Y, c6y, S.n0, S.n1, S.n2, S.dOm);
+    }
+    if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, src, S.E, T(1), P3);
     __syncthreads();
     // the remapped rows (this thread's own bins), with the mixed path's
-    // partials of the exact-total correction: total and largest bin
-    ff partc = ff{0.0f, 0.0f};
-    float bk = -1.0f;
-    int bi = 0x7fffffff;
+    // partials of the output total and of the largest bin
     if (gact) angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
     if (tb.pole) {
       __syncthreads();
       pole_mean(S.dst, NE, NA, NMU, NPH);
       __syncthreads();
     }
+    ff partc = ff{0.0f, 0.0f};
+    float bk = -1.0f;
+    int bi = 0x7fffffff;
     if (gact) {
-      if (sizeof(T) == 4)
-        for (int i = gc; i < NE; i += nch) {
-          const int q = i * NA + gb;
-          partc = ff_add(partc, two_prod((float)S.dst[q], (float)S.dGam[i]));
-          const float k = fabsf((float)S.dst[q] * (float)S.dGam[i]);
+      for (int i = gc; i < NE; i += nch) {
+        const int q = i * NA + gb;
+        const T d = S.dst[q];
+        if (sizeof(T) == 4) {
+          partc = ff_add(partc, two_prod((float)d, (float)S.dGam[i]));
+          const float k = fabsf((float)d * (float)S.dGam[i]);
           if (k > bk) { bk = k; bi = q; }
         }
+        fz[q] = d * rcY;   // f in the new frame (the correction follows)
+      }
     }
-    int at = -1;
-    ff tot_in = ff{0.0f, 0.0f}, tot = ff{0.0f, 0.0f};
     if (sizeof(T) == 4) {
-      // restore the exact content total of the zone (float gathers round)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         partc = ff_add(partc, ff_shfl_down(partc, o));
@@ -2041,32 +2133,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_time_remap(Tables tb, State st)
         if (k2 > bk || (k2 == bk && i2 < bi)) { bk = k2; bi = i2; }
       }
       if (lane == 0) { pin[kWarps + warp] = partc; pk[warp] = bk; pi[warp] = bi; }
-      __syncthreads();
-      tot_in = pin[0];
-      tot = pin[kWarps];
-      float kb = pk[0];
-      at = pi[0];
-      for (int w = 1; w < kWarps; ++w) {
-        tot_in = ff_add(tot_in, pin[w]);
-        tot = ff_add(tot, pin[kWarps + w]);
-        if (pk[w] > kb || (pk[w] == kb && pi[w] < at)) { kb = pk[w]; at = pi[w]; }
-      }
     }
-    if (gact) {
-      const T u0 = Y.g * (T(1) + (Y.v[0] * S.n0[gb] + Y.v[1] * S.n1[gb] + Y.v[2] * S.n2[gb]));
-      const T cang = c6y * u0 * S.dOm[gb];
-      for (int ip = gc; ip < NE; ip += nch) {
-        const int q = ip * NA + gb;
-        T d = S.dst[q];
-        if (q == at) {
-          // the corrected value of bin `at`, formed once by its owner
-          // (float64 work by every thread, or per bin, would run on GB300's
-          // narrow float64 pipe)
-          const double corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
-          d = (T)((double)d + corr_y);
-        }
-        fz[q] = d / cang;
-      }
+  }
+  if (sizeof(T) == 4) {
+    __syncthreads();
+    if (warp == 0) {
+      const int sp = NS - 1;
+      remap_correct<T>(tb, NW, S.redf + (sp & 1) * 2 * kWarps, S.rkey + (sp & 1) * kWarps, S.ridx + (sp & 1) * kWarps,
+                       S.dst, row(sp), Y, c6y, S.n0, S.n1, S.n2, S.dOm);
     }
   }
 }
@@ -2568,7 +2642,12 @@ int split_occupancy_t(const Tables& tb) {
 template <typename T>
 int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
   size_t sm = remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
-  k_time_remap<T><<<tb.n_zone, kThreads, sm, s>>>(tb, st);
+  // 128 threads per CTA (eight CTAs per SM) while one thread per angle
+  // fits, else 256: more zones in flight hide the per-zone barriers
+  if (tb.n_ang <= 128)
+    k_time_remap<T, 128><<<tb.n_zone, 128, sm, s>>>(tb, st);
+  else
+    k_time_remap<T, 256><<<tb.n_zone, 256, sm, s>>>(tb, st);
   return (int)cudaGetLastError();
 }
 
@@ -2614,8 +2693,10 @@ int prepare_kernels() {
   BT_SET((k_flux_faces<double, 512>));
   BT_SET((k_zone_collide<float>));
   BT_SET((k_zone_collide<double>));
-  BT_SET((k_time_remap<float>));
-  BT_SET((k_time_remap<double>));
+  BT_SET((k_time_remap<float, 128>));
+  BT_SET((k_time_remap<float, 256>));
+  BT_SET((k_time_remap<double, 128>));
+  BT_SET((k_time_remap<double, 256>));
   BT_SET(k_sur_table);
 #undef BT_SET
   return (int)e;
