@@ -608,6 +608,61 @@ def time_fp64_path(prob, dev, steps=5, warmup=3):
     return ms
 
 
+def lts_block(prob, levels=4, macro_steps=3):
+    """Local time stepping (Sec. 5) on one problem, mixed precision: the
+    background changes once per hydro step of 2^(levels-1) finest steps dt0
+    (time remap once), then either 2^(levels-1) global steps of dt0 or one
+    local-time-stepping macro step.  Reports both times per hydro step, the
+    ratio, the share of zone updates the levels leave, and the rel-L1
+    difference of f after the same simulated time (the two are different
+    time integrations: that difference is the time-discretisation one)."""
+    import torch
+    from paper_2003_02845_gb300 import bt
+    K = 1 << (levels - 1)
+    dev = _device_backgrounds(prob)
+    out = {"levels": levels, "hydro_steps": macro_steps}
+    res = {}
+    for mode in ("global", "lts"):
+        stream = torch.cuda.Stream()
+        t = bt.Transport(prob, "mixed", stream=stream)
+        t.set_launch_shape(bt.SHAPE_SPLIT | 256)
+        t.set_background(prob.backgrounds[0])
+        t.set_f(prob.f0)
+        dt0, lev = t.lts_levels(prob.cfl, levels)
+
+        def hydro_step(k):
+            t.set_background_device(*dev[(k + 1) % 2])
+            if mode == "lts":
+                t.step_lts(dt0)
+            else:
+                for _ in range(K):
+                    t.step(dt0)
+
+        hydro_step(0)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for k in range(macro_steps):
+            hydro_step(1 + k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        f = torch.empty(prob.f0.shape, dtype=torch.float32, device="cuda")
+        t.get_f(out=f)
+        res[mode] = {"ms_per_hydro_step": ev0.elapsed_time(ev1) / macro_steps, "f": f}
+        if mode == "lts":
+            cnt = np.bincount(lev, minlength=levels)
+            out["zones_per_level"] = cnt.tolist()
+            out["zone_update_share"] = float(sum(cnt[l] * 2 ** (levels - 1 - l) for l in range(levels))
+                                             / (prob.n_zone * K))
+        t.close()
+    out["ms_per_hydro_step_global"] = res["global"]["ms_per_hydro_step"]
+    out["ms_per_hydro_step_lts"] = res["lts"]["ms_per_hydro_step"]
+    out["speedup"] = out["ms_per_hydro_step_global"] / out["ms_per_hydro_step_lts"]
+    out["rel_l1_vs_global_steps"] = rel_l1(res["lts"]["f"], res["global"]["f"])
+    out["workload"] = prob.name
+    return out
+
+
 class BatchRun:
     """A batch of the config-5 problems in one precision, backgrounds on the
     device, launch shapes autotuned (or fixed)."""
@@ -822,7 +877,12 @@ def run_batch(args, rank, world):
         a3.shape = None
         r3, t3 = single_problem(W.config3(), a3, world, steps=min(args.steps, 10), e2e=False)
         t3.close()
+        try:
+            lts3 = lts_block(W.config3())
+        except Exception as e:   # report, do not lose the line
+            lts3 = {"error": repr(e)}
         res["extra"] = {"config3": {k: r3[k] for k in ("value", "ms_per_step")},
+                        "config3_local_time_stepping": lts3,
                         "config3_launch_shape": r3["config"]["launch_shape"],
                         "config3_roofline": {k: r3["roofline"][k] for k in
                                              ("avg_launch_ms", "face_pass_avg_ms", "zone_pass_avg_ms",

@@ -486,6 +486,39 @@ __device__ __noinline__ A energy_edge(int t, int ne, int na, int b, int m, A wl,
   return energy_edge_inl<T, A>(t, ne, na, b, m, wl, wr, src, p3c);
 }
 
+// products and sums that the compiler may not fuse: code inlined into
+// several kernels (the fused and the split flux forms) must round the same
+// way in each of them
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// The first (top = false) and last (top = true) group's rows for shifts of
+// less than one group (m = 0 or -1) and at least two groups: the clamped
+// taps of energy_edge_inl in closed form, the same terms in the same order
+// (no call, no loop: the common case of every remap)
+template <typename T, typename A>
+__device__ __forceinline__ A energy_edge_fast(bool top, int ne, int na, int b, int m, A wl, A wr, const T* src,
+                                              const T* p3c) {
+  if (!top) {
+    const A s0 = (A)src[b];
+    A acc = mul_rn(mul_rn(wl, (A)p3c[0]), s0);
+    if (m == -1) {
+      acc = add_rn(acc, mul_rn(mul_rn(wl, (A)p3c[1]), (A)src[na + b]));
+      acc = add_rn(acc, mul_rn(mul_rn(wr, (A)p3c[0]), s0));
+    }
+    return acc;
+  }
+  const int t = ne - 1;
+  const A st = (A)src[t * na + b];
+  if (m == -1) return mul_rn(mul_rn(wr, (A)p3c[0]), st);
+  A acc = mul_rn(mul_rn(wl, (A)p3c[0]), st);
+  acc = add_rn(acc, mul_rn(mul_rn(wr, (A)p3c[-1]), (A)src[(t - 1) * na + b]));
+  acc = add_rn(acc, mul_rn(mul_rn(wr, (A)p3c[0]), st));
+  return acc;
+}
+
 template <typename T, typename A, bool kEdgeCall = false>
 __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, int b, int m, T we, const T* src, T* E,
                                               T c, const T* p3c) {
@@ -499,8 +532,9 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
     // edge rows as below.  Same operations in the same order.
     int t = gc;
     if (t == 0) {
-      E[b] = (T)(kEdgeCall ? energy_edge<T, A>(0, ne, na, b, m, wl, wr, src, p3c)
-                           : energy_edge_inl<T, A>(0, ne, na, b, m, wl, wr, src, p3c));
+      E[b] = (T)(ne >= 2 ? energy_edge_fast<T, A>(false, ne, na, b, m, wl, wr, src, p3c)
+                 : kEdgeCall ? energy_edge<T, A>(0, ne, na, b, m, wl, wr, src, p3c)
+                             : energy_edge_inl<T, A>(0, ne, na, b, m, wl, wr, src, p3c));
       t += nch;
     }
     const T* sL = src + (t - m) * na + b;   // tap t - m; the other tap is one row lower
@@ -510,9 +544,8 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
       acc += wri * (A)sL[-na];
       E[t * na + b] = (T)acc;
     }
-    if (t == ne - 1)
-      E[t * na + b] = (T)(kEdgeCall ? energy_edge<T, A>(t, ne, na, b, m, wl, wr, src, p3c)
-                                    : energy_edge_inl<T, A>(t, ne, na, b, m, wl, wr, src, p3c));
+    if (t == ne - 1)   // here t >= 1, so at least two groups
+      E[t * na + b] = (T)energy_edge_fast<T, A>(true, ne, na, b, m, wl, wr, src, p3c);
     return;
   }
   for (int t = gc; t < ne; t += nch) {
@@ -1098,18 +1131,34 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       ft.rdl0 = Fd.z[0] >= 0 ? (T)(1.0 / (Fd.x[1] - Fd.x[0])) : T(0);
       ft.rdl1 = (T)(1.0 / (Fd.x[2] - Fd.x[1]));
       ft.rdl2 = Fd.z[3] >= 0 ? (T)(1.0 / (Fd.x[3] - Fd.x[2])) : T(0);
-      for (int k = 0; k < 4; ++k) ft.c6k[k] = Fd.z[k] >= 0 ? (T)pow6(st.cf[Fd.z[k]]) : T(0);
-      // boosts of the stencil cells and the face, rotations in T
-      Loc<T>* L = S.L + 5 * tid;
-      for (int k = 0; k < 4; ++k)
-        if (Fd.z[k] >= 0) make_loc(L[k], st.v + 3 * Fd.z[k], st.al[Fd.z[k]], st.cf[Fd.z[k]]);
-      make_loc(L[4], Fd.v, Fd.al, Fd.cf);
-      T* G = S.Gs + 36 * tid;
-      for (int k = 0; k < 4; ++k)
-        for (int q = 0; q < 9; ++q) G[9 * k + q] = Fd.G[k] ? (T)Fd.G[k][q] : T(q % 4 == 0 ? 1 : 0);
     }
   }
   __syncthreads();
+  if (MODE != 2) {
+    // the faces' stencil-cell and face boosts, phi^6 and rotations in T, one
+    // item per thread (each item's global loads and float64 conversions
+    // would otherwise queue behind one thread per face)
+    for (int q = tid; q < nface * 41; q += NT) {
+      const int f = q < 5 * nface ? q / 5 : (q - 5 * nface) / 36;
+      const FaceDesc& Fd = S.F[f];
+      if (Fd.type < 0) continue;
+      if (q < 5 * nface) {
+        const int k = q % 5;
+        Loc<T>* L = S.L + 5 * f;
+        if (k == 4) {
+          make_loc(L[4], Fd.v, Fd.al, Fd.cf);
+        } else {
+          const int zz = Fd.z[k];
+          S.FT[f].c6k[k] = zz >= 0 ? (T)pow6(st.cf[zz]) : T(0);
+          if (zz >= 0) make_loc(L[k], st.v + 3 * zz, st.al[zz], st.cf[zz]);
+        }
+      } else {
+        const int e = (q - 5 * nface) % 36, k = e / 9, m = e % 9;
+        S.Gs[36 * f + e] = Fd.G[k] ? (T)Fd.G[k][m] : T(m % 4 == 0 ? 1 : 0);
+      }
+    }
+    __syncthreads();
+  }
   const T* P3 = S.p3 + NE + 1;       // P3[k] = R^(3k)
 
   // stencil rows of (face fi, species si) into SRC: bulk copies by thread 0
