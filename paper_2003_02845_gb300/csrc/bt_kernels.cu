@@ -770,6 +770,7 @@ struct FluxSmem {
   double* wr_r;    // [warps][nang] f* of the warp's collision row   (aliases buf)
   double* wr_i;    // [warps][nang] 1/D per warp row                 (aliases buf)
   double* red;     // [kMaxWarps * 2]
+  double* zsc;     // [8] the zone's float64 scalars of the collision (formed once)
   double* tally;   // [ns][2] outflow N, E of this zone
   double* corr;    // [ns] exact-total correction of dN (mixed)
   ff* corr_f;      // [ns] the same as a double-float
@@ -831,6 +832,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
   BT_TAKE(zrow, double, mode == 1 ? 0 : (size_t)ns * ne * 5);
   BT_TAKE(rowk, ff, mode == 1 ? 0 : (size_t)ns * ne * 4);
   BT_TAKE(red, double, kMaxWarps * 2);
+  BT_TAKE(zsc, double, mode == 1 ? 0 : 8);
   BT_TAKE(tally, double, ns * 2);
   BT_TAKE(corr, double, ns);
   BT_TAKE(corr_f, ff, ns);
@@ -1688,27 +1690,38 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   // --- implicit collision per (species, group) (Sec. 3.5) and moments (Eq. hydrosource)
   //     f* = f + dN / (phi^6 dV u0 dGamma dOmega); D_b = 1 + (ka+ks) tau_b,
   //     J = sum dOm r/D / sum dOm (1 + ka tau)/D, f = (r + ks tau J)/D
-  const double alz = st.al[zone], c6z = pow6(st.cf[zone]), volz = tb.vol[zone];
-  const double rdt = 1.0 / dt;
+  // the zone's float64 scalars, formed once by one thread: float64 divisions
+  // and square roots by every thread of the CTA would queue on GB300's
+  // narrow float64 pipe
+  if (tid == 0) {
+    const double* v = st.v + 3 * zone;
+    const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    S.zsc[0] = 1.0 / sqrt(1.0 - v2);       // gamma
+    S.zsc[1] = st.al[zone];
+    S.zsc[2] = pow6(st.cf[zone]);
+    S.zsc[3] = 1.0 / (S.zsc[2] * tb.vol[zone]);
+    S.zsc[4] = 1.0 / dt;
+  }
+  __syncthreads();
+  const double gz = S.zsc[0], alz = S.zsc[1], c6z = S.zsc[2], rdt = S.zsc[4];
   {
     const double* v = st.v + 3 * zone;
-    double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    double gz = 1.0 / sqrt(1.0 - v2);
     if constexpr (sizeof(T) == 8) {
+      const double rcz = S.zsc[3];
       for (int ang = tid; ang < NA; ang += NT) {
         int j = ang / NPH, k = ang % NPH;
         double nv = v[0] * tb.mu[j] + (v[1] * tb.cph[k] + v[2] * tb.sph[k]) * tb.smu[j];
         double u0 = gz * (1.0 + nv);
         S.zu0[ang] = u0;
         S.ztau[ang] = alz * dt / u0;
-        S.zcn[ang] = 1.0 / (c6z * volz * u0 * tb.dOm[ang]);   // dN is per unit dGamma
+        S.zcn[ang] = rcz / (u0 * tb.dOm[ang]);   // 1/(phi^6 dV u0 dOmega): dN is per unit dGamma
       }
     } else {
       // the mixed solve's per-angle constants in double-float: the two
       // reciprocals per angle by Newton steps on the FP32 pipes instead of
       // float64 divisions (GB300 runs float64 at 1/64 of the float32 rate)
       const ff alzdt = ff_from_d(alz * dt);
-      const ff czone = ff_from_d(1.0 / (c6z * volz));
+      const ff czone = ff_from_d(S.zsc[3]);
       // per-row opacity constants, converted once by one thread per row
       // (float64 work done by all 32 lanes of a row's warp costs 32x on the
       // narrow float64 pipe)
