@@ -345,26 +345,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // species; they are sorted by source angle so the summation order (and the
 // result) is deterministic.
 // ---------------------------------------------------------------------------
+// Angular-list entries in two arrays: the weight (wmu * wphi) and the source
+// angle, 6 bytes an entry in float32 (10 in float64); a remap's list starts
+// at an offset of both (operator+)
 template <typename T>
-struct AEnt {
-  T w;     // angular weight wmu * wphi
-  int b;   // source angle
-  __device__ __forceinline__ T weight() const { return w; }
-  __device__ __forceinline__ void set(T ww, int bb) { w = ww; b = bb; }
-};
-// float64 entries in 12 bytes (the weight's two 32-bit halves and the source
-// angle) instead of a 16-byte padded struct: six remaps' lists of the largest
-// rows then fit the float64 face pass in shared memory
-template <>
-struct AEnt<double> {
-  int lo, hi;
-  int b;
-  __device__ __forceinline__ double weight() const { return __hiloint2double(hi, lo); }
-  __device__ __forceinline__ void set(double ww, int bb) {
-    lo = __double2loint(ww);
-    hi = __double2hiint(ww);
-    b = bb;
-  }
+struct AList {
+  T* w;
+  short* b;
+  __device__ __forceinline__ AList operator+(int o) const { return AList{w + o, b + o}; }
 };
 
 // the angular targets of one source angle in four fixed slots (mu bracket
@@ -397,7 +385,7 @@ __device__ __forceinline__ void ang_targets4(const Wt<T>& W, int nmu, int nph, i
 // Whole block (synchronises at the end).
 template <typename T>
 __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int nmu, int nph, short* off,
-                             unsigned* msk, AEnt<T>* ent) {
+                             unsigned* msk, AList<T> ent) {
   const int tid = threadIdx.x, nt = (int)blockDim.x;
   const int nwd = (na + 31) >> 5;
   for (int q = tid; q < nr * na * nwd; q += nt) msk[q] = 0u;
@@ -450,9 +438,8 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
       int pos = off[r * (na + 1) + tgt[k]];
       for (int w = 0; w < (b >> 5); ++w) pos += __popc(mt[w]);
       pos += __popc(mt[b >> 5] & ((1u << (b & 31)) - 1u));
-      AEnt<T> e;
-      e.set(wa[k], b);
-      ent[r * 4 * na + pos] = e;
+      ent.w[r * 4 * na + pos] = wa[k];
+      ent.b[r * 4 * na + pos] = (short)b;
     }
   }
   __syncthreads();
@@ -571,17 +558,18 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
 // do not split the warp into separate passes.
 template <int RB, typename T, typename A, typename Out>
 __device__ __forceinline__ void angular_block(int t0, int nch, int ne, int na, int e0, int n, int nmax,
-                                              const AEnt<T>* ent, const T* E, Out out) {
+                                              AList<T> ent, const T* E, Out out) {
   A acc[RB];
 #pragma unroll
   for (int j = 0; j < RB; ++j) acc[j] = A(0);
   for (int k = 0; k < nmax; ++k) {
     if (k < n) {
-      const AEnt<T> e = ent[e0 + k];
+      const A w = (A)ent.w[e0 + k];
+      const int bs = ent.b[e0 + k];
 #pragma unroll
       for (int j = 0; j < RB; ++j) {
         const int t = t0 + j * nch;
-        if (t < ne) acc[j] += (A)e.weight() * (A)E[t * na + e.b];
+        if (t < ne) acc[j] += w * (A)E[t * na + bs];
       }
     }
   }
@@ -599,7 +587,7 @@ __device__ __forceinline__ void angular_block(int t0, int nch, int ne, int na, i
 // slower), those of 512 take RB = 0 (two rows per thread on 80 angles and 12
 // groups, five on 128 angles and 20 groups).
 template <typename T, typename A, int RB = 4, typename Out>
-__device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int e0, int e1, const AEnt<T>* ent,
+__device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int e0, int e1, AList<T> ent,
                                              const T* E, Out out) {
   const int n = e1 - e0;
   const int nmax = __reduce_max_sync(__activemask(), n);
@@ -786,7 +774,7 @@ struct FluxSmem {
   T* buf;          // [8][ne][nang]: 4 stencil/g buffers, 4 work buffers
   Wt<T>* W;        // [6][nang]   (aliases the work buffers)
   unsigned* msk;   // [6][nang][ceil(nang/32)] (aliases the work buffers)
-  AEnt<T>* ent;    // [6][4 nang]
+  AList<T> ent;    // [6][4 nang]
   short* off;      // [6][nang + 1]
   T* n0; T* n1; T* n2;  // [nang] direction components
   T* dOm;          // [nang]
@@ -867,7 +855,8 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     }
     o = o_b + tot;
   }
-  BT_TAKE(ent, AEnt<T>, mode == 2 ? 0 : 6 * 4 * nang);
+  BT_TAKE(ent.w, T, mode == 2 ? 0 : 6 * 4 * nang);
+  BT_TAKE(ent.b, short, mode == 2 ? 0 : 6 * 4 * nang);
   BT_TAKE(off, short, mode == 2 ? 0 : 6 * (nang + 1));
   BT_TAKE(n0, T, nang);
   BT_TAKE(n1, T, nang);
@@ -1536,7 +1525,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         for (int side = 0; side < 2; ++side) {
           if (!(side == 0 ? depP : depQ)) continue;
           const short* off = S.off + (4 + side) * (NA + 1);
-          const AEnt<T>* ent = S.ent + (4 + side) * 4 * NA;
+          const AList<T> ent = S.ent + (4 + side) * 4 * NA;
           const T* Es = side == 0 ? EP : EQ;
           const T sgn = side == 0 ? T(-1) : T(1);
           if (MODE == 0) {
@@ -1940,7 +1929,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
 // CTAs fit an SM (64 registers, no spills); 512-thread CTAs are for large
 // rows, where shared memory allows one or two per SM anyway
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 1024 / NT) : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 2 : 1024 / NT) : 1)
     k_flux_faces(Tables tb, State st, double dt, T* dep, DepRec* rec) {
   flux_body<T, NT, 1>(tb, st, dt, dep, rec);
 }
@@ -1956,7 +1945,7 @@ template <typename T>
 struct RemapSmem {
   T* src[2];   // species rows (bulk copies; converted in place to content per dGamma), double-buffered
   T* E; T* dst; T* mu; T* n0; T* n1; T* n2; T* dOm; T* dGam; T* p3;
-  Wt<T>* W; AEnt<T>* ent; short* off; unsigned* msk;
+  Wt<T>* W; AList<T> ent; short* off; unsigned* msk;
   ff* redf; float* rkey; int* ridx;
   unsigned long long* bar;   // [2] mbarriers of the two row buffers
   Loc<T>* L;                 // [2] the old and the new background of the zone
@@ -1985,7 +1974,8 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(dGam, T, ne);
   BT_TAKE(p3, T, 2 * ne + 3);
   BT_TAKE(W, Wt<T>, nang);
-  BT_TAKE(ent, AEnt<T>, 4 * nang);
+  BT_TAKE(ent.w, T, 4 * nang);
+  BT_TAKE(ent.b, short, 4 * nang);
   BT_TAKE(off, short, nang + 1);
   BT_TAKE(msk, unsigned, (size_t)nang * ((nang + 31) / 32));
   BT_TAKE(redf, ff, 4 * kWarps);     // [species parity][input, output total][warp]
