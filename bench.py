@@ -168,7 +168,7 @@ def host_cpu():
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one flux
-# launch from an ncu capture of this bench's small invocation, keyed by
+# step from an ncu capture of the profiling driver's run, keyed by
 # workload, precision and launch shape, and valid only for the kernel code
 # it was taken on (a fingerprint of bt_kernels.cu without its comments and
 # blank lines): changed kernel code reports null until re-captured.
@@ -176,8 +176,13 @@ def host_cpu():
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (208.30e6 + 1079.68e6 + 1343.23e6 + 213.29e6,
-         "66e714065ec8e1e4aea82c38d28894f52b7261fc94a6273a118ebec40c77eb44"),
+        (205.86e6 + 1080.82e6 + 1348.36e6 + 213.96e6, "a5f38f4f883273cb35cd8e14e7b100c76874d8c17d0de638c0f6df3661d583fd"),
+    # captured on the same problem at 128 x 32 zones (python -m
+    # paper_2003_02845_gb300.profiling config5_largest_128x32 mixed split/256 3)
+    # and scaled by the 16x zones of the full 512 x 128 grid (the traffic of
+    # both passes is per zone)
+    ("config5_p2_512x128x20x128x6", "mixed", "split/256"):
+        (16 * (498.72e6 + 1454.76e6 + 1770.26e6 + 260.77e6), "a5f38f4f883273cb35cd8e14e7b100c76874d8c17d0de638c0f6df3661d583fd"),
 }
 
 
