@@ -208,7 +208,11 @@ int bt_step_lts(bt_handle* h, double dt0);
 /* Collision source terms of the last step (Eq. hydrosource), per unit
  * coordinate volume and time: dN[s][zone], dE[s][zone] (comoving energy),
  * dP[s][zone][3] (comoving momentum, local triad), Q_Ye[zone] =
- * -(dN_nue - dN_nuebar) * phase_norm.  Any output may be NULL. */
+ * -(dN_nue - dN_nuebar) * phase_norm.  Any output may be NULL.
+ * Sign: dN, dE and dP are what the neutrinos gain from collisions (+ when
+ * emission exceeds absorption); the hydro source terms Q_E and Q_M of Eq.
+ * hydrosource are their negatives summed over species, which the caller
+ * forms.  Q_Ye is returned with the equation's sign already applied. */
 int bt_moments(bt_handle* h, int mem, double* dN, double* dE, double* dP, double* Q_Ye);
 
 /* Per-species totals (host arrays of n_species): number N = sum dV phi^6 u^0
