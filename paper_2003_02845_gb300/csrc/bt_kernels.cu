@@ -580,8 +580,8 @@ __device__ __forceinline__ void angular_block(int t0, int nch, int ne, int na, i
   }
 }
 
-// RB = 4: rows in blocks of four.  RB = 0: blocks of four while four rows
-// remain, then of two, then single rows (no masked-off rows in a block).
+// RB = 2, 4 or 5: rows in blocks of RB.  RB = 0: blocks of four while four
+// rows remain, then of two, then single rows (no masked-off rows in a block).
 // Kernels of up to 256 threads per CTA take RB = 4 (three or more rows per
 // thread at the usual sizes; the longer code of RB = 0 made their bodies
 // slower), those of 512 take RB = 0 (two rows per thread on 80 angles and 12
@@ -591,8 +591,8 @@ __device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, in
                                              const T* E, Out out) {
   const int n = e1 - e0;
   const int nmax = __reduce_max_sync(__activemask(), n);
-  if (RB == 4) {
-    for (int t0 = gc; t0 < ne; t0 += 4 * nch) angular_block<4, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
+  if constexpr (RB > 0) {
+    for (int t0 = gc; t0 < ne; t0 += RB * nch) angular_block<RB, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
   } else {
     int t0 = gc;
     for (; t0 + 3 * nch < ne; t0 += 4 * nch) angular_block<4, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
@@ -808,7 +808,7 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     o += sizeof(type) * (size_t)(count);                       \
   } while (0)
   BT_TAKE(bar, unsigned long long, 2);
-  BT_TAKE(dN, typename DNT<T>::type, mode == 1 ? 0 : (size_t)ns * nbin);   // the face pass keeps no dN
+  BT_TAKE(dN, typename DNT<T>::type, mode == 0 ? (size_t)ns * nbin : 0);   // fused kernel only
   const int nz_ang = mode == 1 ? 0 : nang;   // the collision's arrays: not in the face pass
   BT_TAKE(zu0, double, nz_ang);
   BT_TAKE(ztau, double, nz_ang);
@@ -1037,7 +1037,9 @@ struct AddDN {   // dN += sign * T[F]
   __device__ void operator()(int t, T acc) const { dn[t * na + b] += (typename DNT<T>::type)(sign * acc); }
 };
 
-template <typename T, int NT, int MODE>
+// RB: rows per angular-list walk (angular_rows); the default is the one the
+// fused kernel and the zone pass use
+template <typename T, int NT, int MODE, int RB = (NT >= 512 ? 0 : 4)>
 __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, double dt, T* dep, DepRec* rec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using DN = typename DNT<T>::type;
@@ -1064,8 +1066,10 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   unsigned tphase = 0;               // parity of the next mbarrier phase to wait for
   const T dtT = (T)dt;               // converted once
 
-  if (MODE != 1)
+  if (MODE == 0)
     for (int q = tid; q < NS * nbin; q += NT) S.dN[q] = DN(0);
+  // the zone's summed deposits [s][group][angle]: shared memory in the fused
+  // kernel; in the zone pass, the zone's first deposit slot (set below)
   if constexpr (sizeof(T) == 4) {
     // the float32 tables (no per-CTA float64 conversions)
     for (int q = tid; q < NMU; q += NT) S.mu[q] = tb.f_mu[q];
@@ -1315,7 +1319,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           if (k == 0 && F.type != F_INTERNAL) continue;
           const short* off = S.off + slot * (NA + 1);
           StoreG<T> st_g{SRC + slot * nbin, csb, NA, gb};
-          angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
+          angular_rows<T, T, RB>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
         }
       }
       __syncthreads();
@@ -1529,11 +1533,11 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           const T* Es = side == 0 ? EP : EQ;
           const T sgn = side == 0 ? T(-1) : T(1);
           if (MODE == 0) {
-            angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es,
+            angular_rows<T, T, RB>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es,
                                AddDN<T>{S.dN + (size_t)s * nbin, NA, gb, sgn});
           } else {
             T* d = dep + (((size_t)F.z[1 + side] * 6 + 2 * F.axis + (side == 0 ? 1 : 0)) * NS + s) * nbin;
-            angular_rows<T, T, (NT >= 512 ? 0 : 4)>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn, side == 0 ? F.addP != 0 : F.addQ != 0});
+            angular_rows<T, T, RB>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn, side == 0 ? F.addP != 0 : F.addQ != 0});
           }
         }
       }
@@ -1549,6 +1553,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
     pole_mean(S.dN, NS * NE, NA, NMU, NPH);
     __syncthreads();
   }
+  DN* dNall = S.dN;
   if constexpr (MODE == 2) {
     // gather this zone's deposits in the fused kernel's order: faces in
     // order; per face the rows P side then Q side, the exact totals Q side
@@ -1562,6 +1567,12 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       if (isP) rows[nrow++] = 2 * axis + 1;
       if (isQ) rows[nrow++] = 2 * axis;
     }
+    // the sums go to the zone's first slot: each element is written by the
+    // thread that has just read all of its rows, and no other zone reads
+    // this zone's slots (the next face pass rewrites them before they are
+    // read again), so shared memory holds no species-sized rows and more
+    // CTAs fit on an SM
+    dNall = dep + ((size_t)zone * 6 + rows[0]) * NS * nbin;
     // exact totals and outflow tallies of the zone's records
     if (warp == 0) zone_records(tb, rec, zone, a, b, nface, NS, sizeof(T) == 4, S.dtot, S.tally);
     // all of an element's rows are loaded before they are summed in order
@@ -1581,18 +1592,18 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       // (as the fused kernel does), then find the correction below
       for (int s = 0; s < NS; ++s) {
         const T* base = dep + ((size_t)zone * 6 * NS + s) * nbin;
-        DN* dNs = S.dN + (size_t)s * nbin;
+        DN* dNs = dNall + (size_t)s * nbin;
         for (int q = tid; q < nbin; q += NT) dNs[q] = gather(base, q);
       }
       __syncthreads();
-      pole_mean(S.dN, NS * NE, NA, NMU, NPH);
+      pole_mean(dNall, NS * NE, NA, NMU, NPH);
       __syncthreads();
     }
     for (int s = 0; s < NS; ++s) {
       // the mixed path's exact-total correction is found in the gathering
       // pass (or, with pole nodes, in a pass over the spread sums)
       const T* base = dep + ((size_t)zone * 6 * NS + s) * nbin;
-      DN* dNs = S.dN + (size_t)s * nbin;
+      DN* dNs = dNall + (size_t)s * nbin;
       ff part = ff{0.0f, 0.0f};
       float bk = -1.0f;
       int bi = 0x7fffffff;
@@ -1739,7 +1750,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   for (int row = warp; row < NS * NE; row += (NT / 32)) {
     const int s = row / NE, i = row % NE;
     const T* fz = fin + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
-    const DN* dn = S.dN + (size_t)s * nbin + (size_t)i * NA;
+    const DN* dn = dNall + (size_t)s * nbin + (size_t)i * NA;
     const int cat = S.corr_at[s] - i * NA;       // corrected bin of this row, if any
     T* fo = fout + ((size_t)s * tb.n_zone + zone) * nbin + (size_t)i * NA;
     double mN = 0.0, mE = 0.0, mP0 = 0.0, mP1 = 0.0, mP2 = 0.0;
@@ -1928,10 +1939,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
 // the face pass keeps no dN or collision arrays: in float32 four 256-thread
 // CTAs fit an SM (64 registers, no spills); 512-thread CTAs are for large
 // rows, where shared memory allows one or two per SM anyway
-template <typename T, int NT>
+// RB: rows per angular-list walk, chosen per problem by face_rb (the
+// results do not depend on it: every row sums its list in the same order)
+template <typename T, int NT, int RB = (NT >= 512 ? 0 : 4)>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 2 : 1024 / NT) : 1)
     k_flux_faces(Tables tb, State st, double dt, T* dep, DepRec* rec) {
-  flux_body<T, NT, 1>(tb, st, dt, dep, rec);
+  flux_body<T, NT, 1, RB>(tb, st, dt, dep, rec);
 }
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_zone_collide(Tables tb, State st, double dt, T* dep, DepRec* rec) {
@@ -2659,12 +2672,45 @@ int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) 
 }
 
 // split form: the face pass, then the zone pass (both one CTA per zone)
+// rows per angular-list walk of the float32 face pass: each thread's rows
+// (rows = groups / (threads / angles), rounded up) in as few walks as
+// possible without rows masked off -- five rows a walk where the count is a
+// multiple of five (20 groups on 128 angles: two walks instead of three),
+// two where a thread has at most two
+template <int NT>
+int face_rb(const Tables& tb) {
+  const int nch = NT / tb.n_ang > 0 ? NT / tb.n_ang : 1;
+  const int rows = (tb.n_e + nch - 1) / nch;
+  if (rows % 5 == 0) return 5;
+  if (NT < 512 && rows <= 2) return 2;
+  return NT >= 512 ? 0 : 4;
+}
 template <typename T, int NT>
 int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void* rec, cudaStream_t s) {
   size_t sm1 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 1, nullptr, nullptr);
   const int grid = st.zlist ? st.n_zlist : tb.n_zone;
   if (grid <= 0) return 0;
-  k_flux_faces<T, NT><<<grid, NT, sm1, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
+  T* d = reinterpret_cast<T*>(dep);
+  DepRec* r = reinterpret_cast<DepRec*>(rec);
+  // (the float64 face pass is bound by the float64 pipe: one variant)
+  const int rb = sizeof(T) == 4 ? face_rb<NT>(tb) : -1;
+  if constexpr (sizeof(T) == 4 && NT == 256) {
+    if (rb == 5) {
+      k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+    if (rb == 2) {
+      k_flux_faces<T, NT, 2><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+  }
+  if constexpr (sizeof(T) == 4 && NT == 512) {
+    if (rb == 5) {
+      k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+  }
+  k_flux_faces<T, NT><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
   return (int)cudaGetLastError();
 }
 template <typename T>
@@ -2740,7 +2786,10 @@ int prepare_kernels() {
   BT_SET((k_flux_collide<double, 256>));
   BT_SET((k_flux_collide<double, 512>));
   BT_SET((k_flux_faces<float, 256>));
+  BT_SET((k_flux_faces<float, 256, 5>));
+  BT_SET((k_flux_faces<float, 256, 2>));
   BT_SET((k_flux_faces<float, 512>));
+  BT_SET((k_flux_faces<float, 512, 5>));
   BT_SET((k_flux_faces<double, 256>));
   BT_SET((k_flux_faces<double, 512>));
   BT_SET((k_zone_collide<float>));
