@@ -445,6 +445,27 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
   __syncthreads();
 }
 
+// Layout of the energy pass's output (the angular pass's input): a thread
+// of chunk gc handles rows t = gc + k nch (k = 0, 1, ...) of its column;
+// those rows of column b are contiguous, E[(gc na + b) rpt + k], so that the
+// angular pass reads a block of rows of one source angle at immediate
+// offsets from one address.  rpt: the rows of a chunk rounded up to whole
+// blocks of rb, and to an odd count (consecutive columns then fall in
+// different shared-memory banks).
+__host__ __device__ __forceinline__ int chunk_nch(int na, int nt) { return nt / na > 0 ? nt / na : 1; }
+__host__ __device__ __forceinline__ int chunk_rpt(int ne, int na, int nt, int rb) {
+  const int nch = chunk_nch(na, nt);
+  const int rows = (ne + nch - 1) / nch;
+  int r = (rows + rb - 1) / rb * rb;
+  return (r & 1) ? r : r + 1;
+}
+// elements of one energy-pass output buffer (at least ne na, a multiple of 4)
+__host__ __device__ __forceinline__ size_t chunk_elems(int ne, int na, int nt, int rb) {
+  size_t n = (size_t)chunk_nch(na, nt) * na * chunk_rpt(ne, na, nt, rb);
+  if (n < (size_t)ne * na) n = (size_t)ne * na;
+  return (n + 3) & ~size_t(3);
+}
+
 // Energy pass for column b (source angle b, shift m, upper weight we) in
 // "y-form" (content per unit dGamma): source group i goes to groups
 // clamp(i+m) (weight 1-we) and clamp(i+m+1) (we), and its content per unit
@@ -506,9 +527,11 @@ __device__ __forceinline__ A energy_edge_fast(bool top, int ne, int na, int b, i
   return acc;
 }
 
+// (src: rows [group][angle]; E: the chunk layout above, rpt its row count)
 template <typename T, typename A, bool kEdgeCall = false>
 __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, int b, int m, T we, const T* src, T* E,
-                                              T c, const T* p3c) {
+                                              int rpt, T c, const T* p3c) {
+  T* Ec = E + (size_t)(gc * na + b) * rpt;   // row t = gc + k nch at Ec[k]
   const A wl = (A)c * (A(1) - (A)we), wr = (A)c * (A)we;
   const bool small = m > -ne && m < ne;   // interior sources exist only then
   const A wli = small ? wl * (A)p3c[-m] : A(0);
@@ -518,10 +541,11 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
     // interior row lie in range, so the rows need no bounds checks; the
     // edge rows as below.  Same operations in the same order.
     int t = gc;
+    T* Ek = Ec;
     if (t == 0) {
-      E[b] = (T)(ne >= 2 ? energy_edge_fast<T, A>(false, ne, na, b, m, wl, wr, src, p3c)
-                 : kEdgeCall ? energy_edge<T, A>(0, ne, na, b, m, wl, wr, src, p3c)
-                             : energy_edge_inl<T, A>(0, ne, na, b, m, wl, wr, src, p3c));
+      *Ek++ = (T)(ne >= 2 ? energy_edge_fast<T, A>(false, ne, na, b, m, wl, wr, src, p3c)
+                  : kEdgeCall ? energy_edge<T, A>(0, ne, na, b, m, wl, wr, src, p3c)
+                              : energy_edge_inl<T, A>(0, ne, na, b, m, wl, wr, src, p3c));
       t += nch;
     }
     const T* sL = src + (t - m) * na + b;   // tap t - m; the other tap is one row lower
@@ -529,13 +553,13 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
       A acc = A(0);
       acc += wli * (A)sL[0];
       acc += wri * (A)sL[-na];
-      E[t * na + b] = (T)acc;
+      *Ek++ = (T)acc;
     }
     if (t == ne - 1)   // here t >= 1, so at least two groups
-      E[t * na + b] = (T)energy_edge_fast<T, A>(true, ne, na, b, m, wl, wr, src, p3c);
+      *Ek = (T)energy_edge_fast<T, A>(true, ne, na, b, m, wl, wr, src, p3c);
     return;
   }
-  for (int t = gc; t < ne; t += nch) {
+  for (int t = gc, k = 0; t < ne; t += nch, ++k) {
     A acc = A(0);
     if (t > 0 && t < ne - 1) {
       int iL = t - m, iR = t - m - 1;
@@ -546,31 +570,31 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
     } else {
       acc = energy_edge_inl<T, A>(t, ne, na, b, m, wl, wr, src, p3c);
     }
-    E[t * na + b] = (T)acc;
+    Ec[k] = (T)acc;
   }
 }
 
 // Angular pass for destination angle bp over the rows of this thread:
 // out(t) = sum_e w_e E[t][b_e], the entries summed in list order.  Rows are
-// taken RB at a time and each list entry is read once for the RB rows; the
-// lanes of a warp walk the entries together up to the longest list among
+// taken RB at a time and each list entry is read once for the RB rows, whose
+// values of its source angle are contiguous in the chunk layout (Eb: the
+// block's first row of source angle 0; a source's rows at Eb + b rpt + j).
+// The lanes of a warp walk the entries together up to the longest list among
 // them (a lane with a shorter list skips the rest), so lists of uneven length
-// do not split the warp into separate passes.
+// do not split the warp into separate passes.  Rows past the last group
+// (padding of the block) are read but never stored.
 template <int RB, typename T, typename A, typename Out>
-__device__ __forceinline__ void angular_block(int t0, int nch, int ne, int na, int e0, int n, int nmax,
-                                              AList<T> ent, const T* E, Out out) {
+__device__ __forceinline__ void angular_block(int t0, int nch, int ne, const T* Eb, int rpt, int e0, int n, int nmax,
+                                              AList<T> ent, Out out) {
   A acc[RB];
 #pragma unroll
   for (int j = 0; j < RB; ++j) acc[j] = A(0);
   for (int k = 0; k < nmax; ++k) {
     if (k < n) {
       const A w = (A)ent.w[e0 + k];
-      const int bs = ent.b[e0 + k];
+      const T* eb = Eb + ent.b[e0 + k] * rpt;
 #pragma unroll
-      for (int j = 0; j < RB; ++j) {
-        const int t = t0 + j * nch;
-        if (t < ne) acc[j] += w * (A)E[t * na + bs];
-      }
+      for (int j = 0; j < RB; ++j) acc[j] += w * (A)eb[j];
     }
   }
 #pragma unroll
@@ -580,25 +604,16 @@ __device__ __forceinline__ void angular_block(int t0, int nch, int ne, int na, i
   }
 }
 
-// RB = 2, 4 or 5: rows in blocks of RB.  RB = 0: blocks of four while four
-// rows remain, then of two, then single rows (no masked-off rows in a block).
-// Kernels of up to 256 threads per CTA take RB = 4 (three or more rows per
-// thread at the usual sizes; the longer code of RB = 0 made their bodies
-// slower), those of 512 take RB = 0 (two rows per thread on 80 angles and 12
-// groups, five on 128 angles and 20 groups).
-template <typename T, typename A, int RB = 4, typename Out>
-__device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int e0, int e1, AList<T> ent,
+// RB rows per walk of the lists (the kernels pick it from the rows a thread
+// holds); E in the chunk layout with rpt rows per column
+template <typename T, typename A, int RB, typename Out>
+__device__ __forceinline__ void angular_rows(int gc, int nch, int ne, int na, int rpt, int e0, int e1, AList<T> ent,
                                              const T* E, Out out) {
   const int n = e1 - e0;
   const int nmax = __reduce_max_sync(__activemask(), n);
-  if constexpr (RB > 0) {
-    for (int t0 = gc; t0 < ne; t0 += RB * nch) angular_block<RB, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
-  } else {
-    int t0 = gc;
-    for (; t0 + 3 * nch < ne; t0 += 4 * nch) angular_block<4, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
-    for (; t0 + nch < ne; t0 += 2 * nch) angular_block<2, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
-    for (; t0 < ne; t0 += nch) angular_block<1, T, A>(t0, nch, ne, na, e0, n, nmax, ent, E, out);
-  }
+  const T* Eg = E + (size_t)gc * na * rpt;
+  for (int t0 = gc, blk = 0; t0 < ne; t0 += RB * nch, ++blk)
+    angular_block<RB, T, A>(t0, nch, ne, Eg + blk * RB, rpt, e0, n, nmax, ent, out);
 }
 
 // Pole nodes of a Gauss-Lobatto mu grid (mu = -1 and +1): the n_ph cells of
@@ -796,8 +811,12 @@ struct FluxSmem {
   T* p3;           // [2 ne + 3] R^(3k)
 };
 
+// rows per angular-list walk (RB) of a kernel of nt threads, unless the
+// launch picks another (face_rb)
+__host__ __device__ constexpr int default_rb(int nt) { return nt >= 512 ? 2 : 4; }
+
 template <typename T>
-__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, int nw, int mode, FluxSmem<T>* s,
+__host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, int nw, int mode, int rb, FluxSmem<T>* s,
                                            unsigned char* base) {
   size_t o = 0;
   const int nbin = ne * nang;
@@ -840,7 +859,8 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     size_t stencil = sizeof(T) * (size_t)4 * nbin;
     size_t o_work = o_b + stencil;
     size_t o_c = (o_work + sizeof(Wt<T>) * (size_t)6 * nang + 15) & ~size_t(15);
-    size_t need_work = sizeof(T) * (size_t)4 * nbin;
+    // the work buffers hold the energy passes' outputs in the chunk layout
+    size_t need_work = sizeof(T) * (size_t)4 * chunk_elems(ne, nang, nw * 32, rb);
     size_t need_wc = o_c + sizeof(unsigned) * (size_t)6 * nang * ((nang + 31) / 32) - o_work;
     size_t need_col = sizeof(double) * (size_t)2 * nw * nang;
     size_t tot = stencil + (need_work > need_wc ? need_work : need_wc);
@@ -1039,12 +1059,12 @@ struct AddDN {   // dN += sign * T[F]
 
 // RB: rows per angular-list walk (angular_rows); the default is the one the
 // fused kernel and the zone pass use
-template <typename T, int NT, int MODE, int RB = (NT >= 512 ? 0 : 4)>
+template <typename T, int NT, int MODE, int RB = default_rb(NT)>
 __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, double dt, T* dep, DepRec* rec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using DN = typename DNT<T>::type;
   FluxSmem<T> S;
-  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, MODE, &S, smem_raw);
+  flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, MODE, RB, &S, smem_raw);
   const int zone = st.zlist ? st.zlist[blockIdx.x] : (int)blockIdx.x;
   const int a = zone % tb.n_r, b = zone / tb.n_r;
   // local time stepping: the zone pass takes the zone's own step
@@ -1060,7 +1080,9 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   const T* fin = reinterpret_cast<const T*>(st.f);
   T* fout = reinterpret_cast<T*>(st.f_next);
   T* const SRC = S.buf;              // [4] stencil f rows (TMA), then g (face f values)
-  T* const EB = S.buf + 4 * nbin;    // [4] work buffers
+  T* const EB = S.buf + 4 * nbin;    // [4] work buffers of ebs elements
+  const int ebs = (int)chunk_elems(NE, NA, NT, RB);
+  const int rpt = chunk_rpt(NE, NA, NT, RB);   // rows per column in the chunk layout
   const unsigned rowbytes = (unsigned)(sizeof(T) * (size_t)nbin);
   const bool use_tma = (rowbytes % 16u) == 0u;
   unsigned tphase = 0;               // parity of the next mbarrier phase to wait for
@@ -1299,7 +1321,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
             const int m = slot == 0 ? em[0] : slot == 1 ? em[1] : slot == 2 ? em[2] : em[3];
             const T we = slot == 0 ? ew[0] : slot == 1 ? ew[1] : slot == 2 ? ew[2] : ew[3];
             const T c = slot == 0 ? cang[0] : slot == 1 ? cang[1] : slot == 2 ? cang[2] : cang[3];
-            energy_column<T, T, true>(gc, nch, NE, NA, gb, m, we, SRC + slot * nbin, EB + slot * nbin, c, P3);
+            energy_column<T, T, true>(gc, nch, NE, NA, gb, m, we, SRC + slot * nbin, EB + slot * ebs, rpt, c, P3);
           }
       }
       __syncthreads();
@@ -1319,7 +1341,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           if (k == 0 && F.type != F_INTERNAL) continue;
           const short* off = S.off + slot * (NA + 1);
           StoreG<T> st_g{SRC + slot * nbin, csb, NA, gb};
-          angular_rows<T, T, RB>(gc, nch, NE, NA, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * nbin, st_g);
+          angular_rows<T, T, RB>(gc, nch, NE, NA, rpt, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * ebs, st_g);
         }
       }
       __syncthreads();
@@ -1345,8 +1367,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       const T* G2 = SRC + 2 * nbin;
       const T* G3 = SRC + 3 * nbin;
       T* RD = EB;                 // r / D
-      T* FL = EB + nbin;          // flux content
-      T* ID = EB + 2 * nbin;      // 1 / D
+      T* FL = EB + ebs;           // flux content
+      T* ID = EB + 2 * ebs;       // 1 / D
       // Lax-Wendroff half step with implicit collision [R-10]: per bin
       // r = (g1+g2)/2 - (dt/2) v (g2-g1)/dx + tau ka feq, D = 1 + (ka+ks) tau
       if (F.type == F_INTERNAL) {
@@ -1513,15 +1535,15 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         }
       }
       // deposits into this zone: dN -= T_{s->P}[F] (own P), dN += T_{s->Q}[F] (own Q)
-      T* EP = EB + 2 * nbin;
-      T* EQ = EB + 3 * nbin;
+      T* EP = EB + 2 * ebs;
+      T* EQ = EB + 3 * ebs;
       // one code path for both sides (P first): a smaller kernel body
       if (gact) {
 #pragma unroll 1
         for (int side = 0; side < 2; ++side)
           if (side == 0 ? depP : depQ)
             energy_column<T, T, true>(gc, nch, NE, NA, gb, side == 0 ? em[4] : em[5], side == 0 ? ew[4] : ew[5], FL,
-                                side == 0 ? EP : EQ, T(1), P3);
+                                side == 0 ? EP : EQ, rpt, T(1), P3);
       }
       __syncthreads();
       if (gact) {
@@ -1533,11 +1555,11 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           const T* Es = side == 0 ? EP : EQ;
           const T sgn = side == 0 ? T(-1) : T(1);
           if (MODE == 0) {
-            angular_rows<T, T, RB>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es,
+            angular_rows<T, T, RB>(gc, nch, NE, NA, rpt, off[gb], off[gb + 1], ent, Es,
                                AddDN<T>{S.dN + (size_t)s * nbin, NA, gb, sgn});
           } else {
             T* d = dep + (((size_t)F.z[1 + side] * 6 + 2 * F.axis + (side == 0 ? 1 : 0)) * NS + s) * nbin;
-            angular_rows<T, T, RB>(gc, nch, NE, NA, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn, side == 0 ? F.addP != 0 : F.addQ != 0});
+            angular_rows<T, T, RB>(gc, nch, NE, NA, rpt, off[gb], off[gb + 1], ent, Es, StoreDep<T>{d, NA, gb, sgn, side == 0 ? F.addP != 0 : F.addQ != 0});
           }
         }
       }
@@ -1941,7 +1963,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
 // rows, where shared memory allows one or two per SM anyway
 // RB: rows per angular-list walk, chosen per problem by face_rb (the
 // results do not depend on it: every row sums its list in the same order)
-template <typename T, int NT, int RB = (NT >= 512 ? 0 : 4)>
+template <typename T, int NT, int RB = default_rb(NT)>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 2 : 1024 / NT) : 1)
     k_flux_faces(Tables tb, State st, double dt, T* dep, DepRec* rec) {
   flux_body<T, NT, 1, RB>(tb, st, dt, dep, rec);
@@ -1966,7 +1988,7 @@ struct RemapSmem {
 };
 
 template <typename T>
-__host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSmem<T>* s, unsigned char* base) {
+__host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, int nt, RemapSmem<T>* s, unsigned char* base) {
   size_t o = 0;
 #define BT_TAKE(ptr, type, count)                              \
   do {                                                         \
@@ -1977,7 +1999,7 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, RemapSme
   BT_TAKE(bar, unsigned long long, 2);
   BT_TAKE(src[0], T, (size_t)ne * nang);
   BT_TAKE(src[1], T, (size_t)ne * nang);
-  BT_TAKE(E, T, (size_t)ne * nang);
+  BT_TAKE(E, T, chunk_elems(ne, nang, nt, 4));   // the energy pass's output (chunk layout)
   BT_TAKE(dst, T, (size_t)ne * nang);
   BT_TAKE(mu, T, nmu);
   BT_TAKE(n0, T, nang);
@@ -2041,7 +2063,8 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) k_time_remap(Tables tb, State st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RemapSmem<T> S;
-  remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, &S, smem_raw);
+  remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, NT, &S, smem_raw);
+  const int rpt = chunk_rpt(tb.n_e, tb.n_ang, NT, 4);
   constexpr int NW = NT / 32;
   const int zone = blockIdx.x;
   const int NE = tb.n_e, NA = tb.n_ang, NPH = tb.n_ph, NMU = tb.n_mu, NS = tb.n_s;
@@ -2164,11 +2187,11 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) k_time_remap(Tables tb,
       remap_correct<T>(tb, NW, S.redf + (sp & 1) * 2 * kWarps, S.rkey + (sp & 1) * kWarps, S.ridx + (sp & 1) * kWarps,
                        S.dst, row(sp), Y, c6y, S.n0, S.n1, S.n2, S.dOm);
     }
-    if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, src, S.E, T(1), P3);
+    if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, src, S.E, rpt, T(1), P3);
     __syncthreads();
     // the remapped rows (this thread's own bins), with the mixed path's
     // partials of the output total and of the largest bin
-    if (gact) angular_rows<T, T>(gc, nch, NE, NA, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
+    if (gact) angular_rows<T, T, 4>(gc, nch, NE, NA, rpt, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
     if (tb.pole) {
       __syncthreads();
       pole_mean(S.dst, NE, NA, NMU, NPH);
@@ -2666,7 +2689,7 @@ __global__ void __launch_bounds__(kSurT) k_sur_table(Tables tb, State st, const 
 
 template <typename T, int NT>
 int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) {
-  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 0, nullptr, nullptr);
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 0, default_rb(NT), nullptr, nullptr);
   k_flux_collide<T, NT><<<tb.n_zone, NT, sm, s>>>(tb, st, dt);
   return (int)cudaGetLastError();
 }
@@ -2676,37 +2699,35 @@ int launch_flux_t(const Tables& tb, const State& st, double dt, cudaStream_t s) 
 // (rows = groups / (threads / angles), rounded up) in as few walks as
 // possible without rows masked off -- five rows a walk where the count is a
 // multiple of five (20 groups on 128 angles: two walks instead of three),
-// two where a thread has at most two
-template <int NT>
+// two where a thread has at most two.  (Whole blocks also keep the chunk
+// layout's padding, and so the shared memory, small.)
+template <typename T, int NT>
 int face_rb(const Tables& tb) {
-  const int nch = NT / tb.n_ang > 0 ? NT / tb.n_ang : 1;
+  const int nch = chunk_nch(tb.n_ang, NT);
   const int rows = (tb.n_e + nch - 1) / nch;
   if (rows % 5 == 0) return 5;
-  if (NT < 512 && rows <= 2) return 2;
-  return NT >= 512 ? 0 : 4;
+  if (sizeof(T) == 4 && NT < 512 && rows <= 2) return 2;
+  return default_rb(NT);
+}
+template <typename T, int NT>
+size_t faces_smem(const Tables& tb) {
+  return flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 1, face_rb<T, NT>(tb), nullptr, nullptr);
 }
 template <typename T, int NT>
 int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void* rec, cudaStream_t s) {
-  size_t sm1 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 1, nullptr, nullptr);
+  const size_t sm1 = faces_smem<T, NT>(tb);
   const int grid = st.zlist ? st.n_zlist : tb.n_zone;
   if (grid <= 0) return 0;
   T* d = reinterpret_cast<T*>(dep);
   DepRec* r = reinterpret_cast<DepRec*>(rec);
-  // (the float64 face pass is bound by the float64 pipe: one variant)
-  const int rb = sizeof(T) == 4 ? face_rb<NT>(tb) : -1;
+  const int rb = face_rb<T, NT>(tb);
+  if (rb == 5) {
+    k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+    return (int)cudaGetLastError();
+  }
   if constexpr (sizeof(T) == 4 && NT == 256) {
-    if (rb == 5) {
-      k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
-      return (int)cudaGetLastError();
-    }
     if (rb == 2) {
       k_flux_faces<T, NT, 2><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
-      return (int)cudaGetLastError();
-    }
-  }
-  if constexpr (sizeof(T) == 4 && NT == 512) {
-    if (rb == 5) {
-      k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
       return (int)cudaGetLastError();
     }
   }
@@ -2715,7 +2736,7 @@ int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void
 }
 template <typename T>
 int launch_zone_t(const Tables& tb, const State& st, double dt, void* dep, void* rec, cudaStream_t s) {
-  size_t sm2 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 256 / 32, 2, nullptr, nullptr);
+  size_t sm2 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 256 / 32, 2, default_rb(256), nullptr, nullptr);
   const int grid = st.zlist ? st.n_zlist : tb.n_zone;
   if (grid <= 0) return 0;
   k_zone_collide<T><<<grid, 256, sm2, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
@@ -2724,28 +2745,29 @@ int launch_zone_t(const Tables& tb, const State& st, double dt, void* dep, void*
 
 template <typename T, int NT>
 int flux_occupancy_t(const Tables& tb) {
-  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 0, nullptr, nullptr);
+  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 0, default_rb(NT), nullptr, nullptr);
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_flux_collide<T, NT>, NT, sm) != cudaSuccess) return 0;
   return blocks;
 }
 template <typename T, int NT>
 int split_occupancy_t(const Tables& tb) {
-  size_t sm = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, 1, nullptr, nullptr);
-  int blocks = 0;
+  const size_t sm = faces_smem<T, NT>(tb);
+  int blocks = 0;   // (every RB variant has the same registers)
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_flux_faces<T, NT>, NT, sm) != cudaSuccess) return 0;
   return blocks;
 }
 
 template <typename T>
 int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
-  size_t sm = remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
   // 128 threads per CTA (eight CTAs per SM) while one thread per angle
   // fits, else 256: more zones in flight hide the per-zone barriers
   if (tb.n_ang <= 128)
-    k_time_remap<T, 128><<<tb.n_zone, 128, sm, s>>>(tb, st);
+    k_time_remap<T, 128><<<tb.n_zone, 128, remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, 128, nullptr, nullptr), s>>>(
+        tb, st);
   else
-    k_time_remap<T, 256><<<tb.n_zone, 256, sm, s>>>(tb, st);
+    k_time_remap<T, 256><<<tb.n_zone, 256, remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, 256, nullptr, nullptr), s>>>(
+        tb, st);
   return (int)cudaGetLastError();
 }
 
@@ -2754,22 +2776,25 @@ int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
 size_t flux_smem_bytes(const Tables& tb, int mixed, int nt) {
   const int threads = nt & 0xFFFF;
   if (nt & kShapeSplit) {
-    size_t a = mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 1, nullptr, nullptr)
-                     : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 1, nullptr, nullptr);
-    size_t b = mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, nullptr, nullptr)
-                     : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, nullptr, nullptr);
+    size_t a = threads >= 512 ? (mixed ? faces_smem<float, 512>(tb) : faces_smem<double, 512>(tb))
+                              : (mixed ? faces_smem<float, 256>(tb) : faces_smem<double, 256>(tb));
+    size_t b = mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, 4, nullptr, nullptr)
+                     : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, 4, nullptr, nullptr);
     return a > b ? a : b;
   }
-  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 0, nullptr, nullptr)
-               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 0, nullptr, nullptr);
+  return mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 0, default_rb(threads), nullptr,
+                                         nullptr)
+               : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, threads / 32, 0, default_rb(threads), nullptr,
+                                          nullptr);
 }
 size_t split_dep_bytes(const Tables& tb, int mixed) {
   return (size_t)tb.n_zone * 6 * tb.n_s * tb.n_e * tb.n_ang * (mixed ? 4 : 8);
 }
 size_t split_rec_bytes(const Tables& tb) { return (size_t)tb.n_zone * 6 * tb.n_s * sizeof(DepRec); }
 size_t remap_smem_bytes(const Tables& tb, int mixed) {
-  return mixed ? remap_smem_layout<float>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr)
-               : remap_smem_layout<double>(tb.n_e, tb.n_ang, tb.n_mu, nullptr, nullptr);
+  const int nt = tb.n_ang <= 128 ? 128 : 256;   // the launch's shape (launch_remap_t)
+  return mixed ? remap_smem_layout<float>(tb.n_e, tb.n_ang, tb.n_mu, nt, nullptr, nullptr)
+               : remap_smem_layout<double>(tb.n_e, tb.n_ang, tb.n_mu, nt, nullptr, nullptr);
 }
 // Allow the large dynamic shared-memory carve-outs once (a function
 // attribute, set outside any stream capture).
@@ -2791,7 +2816,9 @@ int prepare_kernels() {
   BT_SET((k_flux_faces<float, 512>));
   BT_SET((k_flux_faces<float, 512, 5>));
   BT_SET((k_flux_faces<double, 256>));
+  BT_SET((k_flux_faces<double, 256, 5>));
   BT_SET((k_flux_faces<double, 512>));
+  BT_SET((k_flux_faces<double, 512, 5>));
   BT_SET((k_zone_collide<float>));
   BT_SET((k_zone_collide<double>));
   BT_SET((k_time_remap<float, 128>));
