@@ -908,12 +908,12 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
 
 template <typename T>
 __device__ __forceinline__ T mc_limiter(T a, T b) {
-  if (a * b <= T(0)) return T(0);
-  T s = a > T(0) ? T(1) : T(-1);
-  T x = fabs(T(2) * a), y = fabs(T(2) * b), z = T(0.5) * fabs(a + b);
+  // symmetric in a and b, bit for bit; no branch (selects)
+  const T s = a > T(0) ? T(1) : T(-1);
+  const T x = fabs(T(2) * a), y = fabs(T(2) * b), z = T(0.5) * fabs(a + b);
   T m = x < y ? x : y;
   m = m < z ? m : z;
-  return s * m;
+  return a * b <= T(0) ? T(0) : s * m;
 }
 
 __device__ __forceinline__ double block_sum2(double v0, double v1, double* red, double& out1) {
@@ -1340,7 +1340,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           if (F.z[slot] < 0) continue;
           if (k == 0 && F.type != F_INTERNAL) continue;
           const short* off = S.off + slot * (NA + 1);
-          StoreG<T> st_g{SRC + slot * nbin, csb, NA, gb};
+          // (both outer cells' values go to the first row: each bin reads one)
+          StoreG<T> st_g{SRC + k * nbin, csb, NA, gb};
           angular_rows<T, T, RB>(gc, nch, NE, NA, rpt, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * ebs, st_g);
         }
       }
@@ -1354,7 +1355,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           const int j = side ? NMU - 1 : 0;
           const int slot = k == 0 ? (S.vns[j * NPH] >= T(0) ? 0 : 3) : k;
           if (F.z[slot] < 0 || (k == 0 && F.type != F_INTERNAL)) continue;
-          T* c = SRC + slot * nbin + t * NA + j * NPH;
+          T* c = SRC + k * nbin + t * NA + j * NPH;
           T sum = T(0);
           for (int kk = 0; kk < NPH; ++kk) sum += c[kk];
           sum = sum / T(NPH);
@@ -1362,10 +1363,9 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         }
         __syncthreads();
       }
-      const T* G0 = SRC;
+      const T* G0 = SRC;          // the outer stencil cell each bin's upwind side reads
       const T* G1 = SRC + nbin;
       const T* G2 = SRC + 2 * nbin;
-      const T* G3 = SRC + 3 * nbin;
       T* RD = EB;                 // r / D
       T* FL = EB + ebs;           // flux content
       T* ID = EB + 2 * ebs;       // 1 / D
@@ -1440,24 +1440,25 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         const int gm = (NMU - 1 - jj) * NPH + kk;   // mirror angle (reflecting wall)
         const bool up = vn >= T(0);
         const T taug = S.taus[gb];
+        // the upwind side's constants (P where the bin moves P -> Q, else
+        // Q), chosen once: the row loop then has no branch on the side, which
+        // differs between the lanes of a warp
+        const T rdlo = up ? ft.rdl0 : ft.rdl2;     // 1 / distance to the outer cell
+        const T sup = up ? ft.sP : ft.sQ;          // distance cell -> face
+        const T* wup = up ? wPs : wQs;             // flux-switch weights
+        const bool has_outer = up ? F.z[0] >= 0 : F.z[3] >= 0;
         for (int i = gc; i < NE; i += nch) {
           const int q = i * NA + gb;
           T fs;
           if (F.type == F_INTERNAL) {
-            const T g1 = G1[q], g2 = G2[q];
+            const T g1 = G1[q], g2 = G2[q], go = G0[q];
             const T flw = RD[q] + ksS[i] * S.rowJ[i] * taug * ID[q];
-            T fu, w;
-            if (up) {
-              T sl = T(0);
-              if (F.z[0] >= 0) sl = mc_limiter((g1 - G0[q]) * ft.rdl0, (g2 - g1) * ft.rdl1);
-              fu = g1 + sl * ft.sP;
-              w = wPs[i];
-            } else {
-              T sl = T(0);
-              if (F.z[3] >= 0) sl = mc_limiter((g2 - g1) * ft.rdl1, (G3[q] - g2) * ft.rdl2);
-              fu = g2 + sl * ft.sQ;
-              w = wQs[i];
-            }
+            // MC-limited slope of the upwind cell (symmetric in its two
+            // differences; no slope next to the grid's edge)
+            const T od = (up ? g1 - go : go - g2) * rdlo;
+            const T sl = has_outer ? mc_limiter(od, (g2 - g1) * ft.rdl1) : T(0);
+            const T fu = (up ? g1 : g2) + sl * sup;
+            const T w = wup[i];
             fs = (T(1) - w) * flw + w * fu;
           } else if (F.type == F_OUTFLOW_P) {
             // incoming bins: vacuum, or the distribution imposed on the open
