@@ -2036,8 +2036,9 @@ __device__ void remap_correct(const Tables& tb, int nw, const ff* pin, const flo
   ff tot = lane < nw ? pin[kWarps + lane] : ff{0.0f, 0.0f};
   float kb = lane < nw ? pk[lane] : -2.0f;
   int at = lane < nw ? pi[lane] : 0x7fffffff;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  int o0 = 1;   // the first shuffle distance that reaches a warp's partial
+  while (2 * o0 < nw) o0 *= 2;
+  for (int o = o0; o > 0; o >>= 1) {
     tot_in = ff_add(tot_in, ff_shfl_down(tot_in, o));
     tot = ff_add(tot, ff_shfl_down(tot, o));
     const float k2 = __shfl_down_sync(0xffffffffu, kb, o);
@@ -2046,10 +2047,14 @@ __device__ void remap_correct(const Tables& tb, int nw, const ff* pin, const flo
   }
   if (lane != 0 || at < 0 || at >= tb.n_e * tb.n_ang) return;
   const int NA = tb.n_ang, b = at % NA;
-  const double corr_y = ff_to_d(ff_add(tot_in, ff_neg(tot))) / tb.dGam[at / NA];
+  // the correction is a rounding-level term: float arithmetic (no float64
+  // division on the block's critical path) keeps it to well below f's own
+  // rounding
+  const ff dc = ff_add(tot_in, ff_neg(tot));
+  const float corr_y = (dc.hi + dc.lo) * tb.f_rdGam[at / NA];
   const T u0 = Y.g * (T(1) + (Y.v[0] * n0[b] + Y.v[1] * n1[b] + Y.v[2] * n2[b]));
   const T rc = T(1) / (c6y * u0 * dOm[b]);
-  fz[at] = (T)((double)dst[at] + corr_y) * rc;
+  fz[at] = (dst[at] + (T)corr_y) * rc;
 }
 
 // Time remap T_{n->n+1} of every zone (Sec. 3.2): old frames -> new frames,
