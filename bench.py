@@ -176,13 +176,13 @@ def host_cpu():
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (205.86e6 + 1080.82e6 + 1348.36e6 + 213.96e6, "a5f38f4f883273cb35cd8e14e7b100c76874d8c17d0de638c0f6df3661d583fd"),
+        (206.08e6 + 1080.37e6 + 1349.81e6 + 396.24e6, "c633f69dcfb25397b37fec2300837ff28c137bfef63de09fb8208aaf98a2fc74"),
     # captured on the same problem at 128 x 32 zones (python -m
-    # paper_2003_02845_gb300.profiling config5_largest_128x32 mixed split/256 3)
+    # paper_2003_02845_gb300.profiling config5_largest_128x32 mixed split/512 3)
     # and scaled by the 16x zones of the full 512 x 128 grid (the traffic of
     # both passes is per zone)
-    ("config5_p2_512x128x20x128x6", "mixed", "split/256"):
-        (16 * (498.72e6 + 1454.76e6 + 1770.26e6 + 260.77e6), "a5f38f4f883273cb35cd8e14e7b100c76874d8c17d0de638c0f6df3661d583fd"),
+    ("config5_p2_512x128x20x128x6", "mixed", "split/512"):
+        (16 * (478.76e6 + 1466.69e6 + 2012.49e6 + 503.93e6), "c633f69dcfb25397b37fec2300837ff28c137bfef63de09fb8208aaf98a2fc74"),
 }
 
 
