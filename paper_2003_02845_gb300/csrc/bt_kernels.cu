@@ -574,6 +574,70 @@ __device__ __forceinline__ void energy_column(int gc, int nch, int ne, int na, i
   }
 }
 
+// energy_column for one remap, not inlined (the rare path of energy_cells)
+template <typename T, typename A>
+__device__ __noinline__ void energy_column_call(int gc, int nch, int ne, int na, int b, int m, T we, const T* src,
+                                                T* E, int rpt, T c, const T* p3c) {
+  energy_column<T, A, true>(gc, nch, ne, na, b, m, we, src, E, rpt, c, p3c);
+}
+
+// The energy pass of up to NC remaps of one source column together (the same
+// source angle b; remap q with its shift m[q], weight we[q], density factor
+// c[q], source rows src[q] and output E[q]; bit q of act: remap q present,
+// the same for the whole block).  Where the shifts of every present remap in
+// the warp are below one group, the rows are walked once for all of them
+// (the same operations per row as energy_column's); otherwise each remap
+// takes energy_column.
+template <int NC, typename T, typename A>
+__device__ __forceinline__ void energy_cells(int gc, int nch, int ne, int na, int b, unsigned act, const int* m,
+                                             const T* we, const T* c, const T* const* src, T* const* E, int rpt,
+                                             const T* p3c) {
+  bool small = true;
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+    if ((act >> q) & 1u) small = small && (m[q] == 0 || m[q] == -1);
+  if (!__all_sync(__activemask(), small) || ne < 2) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if ((act >> q) & 1u) energy_column_call<T, A>(gc, nch, ne, na, b, m[q], we[q], src[q], E[q], rpt, c[q], p3c);
+    return;
+  }
+  A wl[NC], wr[NC], wli[NC], wri[NC];
+  T* Ec[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    wl[q] = (A)c[q] * (A(1) - (A)we[q]);
+    wr[q] = (A)c[q] * (A)we[q];
+    wli[q] = wl[q] * (A)p3c[-m[q]];
+    wri[q] = wr[q] * (A)p3c[-m[q] - 1];
+    Ec[q] = E[q] + (size_t)(gc * na + b) * rpt;   // row t = gc + k nch at Ec[q][k]
+  }
+  int t = gc, k = 0;
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if ((act >> q) & 1u) Ec[q][0] = (T)energy_edge_fast<T, A>(false, ne, na, b, m[q], wl[q], wr[q], src[q], p3c);
+    t += nch;
+    k = 1;
+  }
+  for (; t < ne - 1; t += nch, ++k) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if ((act >> q) & 1u) {
+        const T* sL = src[q] + (t - m[q]) * na + b;   // tap t - m; the other tap one row lower
+        A acc = A(0);
+        acc += wli[q] * (A)sL[0];
+        acc += wri[q] * (A)sL[-na];
+        Ec[q][k] = (T)acc;
+      }
+  }
+  if (t == ne - 1) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if ((act >> q) & 1u) Ec[q][k] = (T)energy_edge_fast<T, A>(true, ne, na, b, m[q], wl[q], wr[q], src[q], p3c);
+  }
+}
+
 // Angular pass for destination angle bp over the rows of this thread:
 // out(t) = sum_e w_e E[t][b_e], the entries summed in list order.  Rows are
 // taken RB at a time and each list entry is read once for the RB rows, whose
@@ -1315,14 +1379,21 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       // kernel body stays smaller and its instruction fetch stalls less;
       // float64, whose float64 pipe is the bound, keeps the four copies)
       if (gact) {
-#pragma unroll (sizeof(T) == 4 ? 1 : 4)
-        for (int slot = 0; slot < 4; ++slot)
-          if (F.z[slot] >= 0 && (F.type == F_INTERNAL || slot == 1 || slot == 2)) {
-            const int m = slot == 0 ? em[0] : slot == 1 ? em[1] : slot == 2 ? em[2] : em[3];
-            const T we = slot == 0 ? ew[0] : slot == 1 ? ew[1] : slot == 2 ? ew[2] : ew[3];
-            const T c = slot == 0 ? cang[0] : slot == 1 ? cang[1] : slot == 2 ? cang[2] : cang[3];
-            energy_column<T, T, true>(gc, nch, NE, NA, gb, m, we, SRC + slot * nbin, EB + slot * ebs, rpt, c, P3);
-          }
+        if constexpr (sizeof(T) == 4) {
+          // the four cells in one walk of the rows
+          unsigned act = 0;
+          for (int slot = 0; slot < 4; ++slot)
+            if (F.z[slot] >= 0 && (F.type == F_INTERNAL || slot == 1 || slot == 2)) act |= 1u << slot;
+          const T* srcs[4] = {SRC, SRC + nbin, SRC + 2 * nbin, SRC + 3 * nbin};
+          T* outs[4] = {EB, EB + ebs, EB + 2 * ebs, EB + 3 * ebs};
+          energy_cells<4, T, T>(gc, nch, NE, NA, gb, act, em, ew, cang, srcs, outs, rpt, P3);
+        } else {
+#pragma unroll
+          for (int slot = 0; slot < 4; ++slot)
+            if (F.z[slot] >= 0 && (F.type == F_INTERNAL || slot == 1 || slot == 2))
+              energy_column<T, T, true>(gc, nch, NE, NA, gb, em[slot], ew[slot], SRC + slot * nbin, EB + slot * ebs,
+                                        rpt, cang[slot], P3);
+        }
       }
       __syncthreads();
       // angular pass: g_k = T_{k->s}[n_k] as face distribution (into SRC)
@@ -1538,13 +1609,22 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       // deposits into this zone: dN -= T_{s->P}[F] (own P), dN += T_{s->Q}[F] (own Q)
       T* EP = EB + 2 * ebs;
       T* EQ = EB + 3 * ebs;
-      // one code path for both sides (P first): a smaller kernel body
+      // both sides in one walk of the rows (float32), or one code path for
+      // both sides (P first): a smaller kernel body
       if (gact) {
+        if constexpr (sizeof(T) == 4) {
+          const unsigned act = (depP ? 1u : 0u) | (depQ ? 2u : 0u);
+          const T ones[2] = {T(1), T(1)};
+          const T* srcs[2] = {FL, FL};
+          T* outs[2] = {EP, EQ};
+          energy_cells<2, T, T>(gc, nch, NE, NA, gb, act, em + 4, ew + 4, ones, srcs, outs, rpt, P3);
+        } else {
 #pragma unroll 1
-        for (int side = 0; side < 2; ++side)
-          if (side == 0 ? depP : depQ)
-            energy_column<T, T, true>(gc, nch, NE, NA, gb, side == 0 ? em[4] : em[5], side == 0 ? ew[4] : ew[5], FL,
-                                side == 0 ? EP : EQ, rpt, T(1), P3);
+          for (int side = 0; side < 2; ++side)
+            if (side == 0 ? depP : depQ)
+              energy_column<T, T, true>(gc, nch, NE, NA, gb, side == 0 ? em[4] : em[5], side == 0 ? ew[4] : ew[5], FL,
+                                        side == 0 ? EP : EQ, rpt, T(1), P3);
+        }
       }
       __syncthreads();
       if (gact) {
