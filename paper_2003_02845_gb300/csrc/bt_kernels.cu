@@ -1123,7 +1123,7 @@ struct AddDN {   // dN += sign * T[F]
 
 // RB: rows per angular-list walk (angular_rows); the default is the one the
 // fused kernel and the zone pass use
-template <typename T, int NT, int MODE, int RB = default_rb(NT)>
+template <typename T, int NT, int MODE, int RB = default_rb(NT), int NEC = 0, int NAC = 0, int NMUC = 0, int NPHC = 0>
 __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, double dt, T* dep, DepRec* rec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using DN = typename DNT<T>::type;
@@ -1134,7 +1134,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
   // local time stepping: the zone pass takes the zone's own step
   const bool lts = st.lev != nullptr;
   if (lts && MODE == 2) dt = st.dt0 * (double)(1 << st.lev[zone]);
-  const int NE = tb.n_e, NA = tb.n_ang, NS = tb.n_s, NPH = tb.n_ph, NMU = tb.n_mu;
+  const int NE = NEC ? NEC : tb.n_e, NA = NAC ? NAC : tb.n_ang, NS = tb.n_s;
+  const int NPH = NPHC ? NPHC : tb.n_ph, NMU = NMUC ? NMUC : tb.n_mu;
   const int nbin = NE * NA;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -2044,10 +2045,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 1 : 768 / NT
 // rows, where shared memory allows one or two per SM anyway
 // RB: rows per angular-list walk, chosen per problem by face_rb (the
 // results do not depend on it: every row sums its list in the same order)
-template <typename T, int NT, int RB = default_rb(NT)>
+template <typename T, int NT, int RB = default_rb(NT), int NEC = 0, int NAC = 0, int NMUC = 0, int NPHC = 0>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 2 : 1024 / NT) : 1)
     k_flux_faces(Tables tb, State st, double dt, T* dep, DepRec* rec) {
-  flux_body<T, NT, 1, RB>(tb, st, dt, dep, rec);
+  flux_body<T, NT, 1, RB, NEC, NAC, NMUC, NPHC>(tb, st, dt, dep, rec);
 }
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_zone_collide(Tables tb, State st, double dt, T* dep, DepRec* rec) {
@@ -2807,6 +2808,28 @@ int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void
   T* d = reinterpret_cast<T*>(dep);
   DepRec* r = reinterpret_cast<DepRec*>(rec);
   const int rb = face_rb<T, NT>(tb);
+  // the benchmark configurations' grids, with the group and angle counts
+  // fixed at compile time (constant strides and trip counts); every other
+  // problem takes the generic kernel below
+  auto grid_is = [&](int ne, int na, int nmu, int nph) {
+    return tb.n_e == ne && tb.n_ang == na && tb.n_mu == nmu && tb.n_ph == nph;
+  };
+  if constexpr (sizeof(T) == 4 && NT == 512) {
+    if (rb == 5 && grid_is(20, 128, 16, 8)) {
+      k_flux_faces<T, NT, 5, 20, 128, 16, 8><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+  }
+  if constexpr (sizeof(T) == 4 && NT == 256) {
+    if (rb == 4 && grid_is(12, 80, 8, 10)) {
+      k_flux_faces<T, NT, 4, 12, 80, 8, 10><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+    if (rb == 2 && grid_is(8, 48, 6, 8)) {
+      k_flux_faces<T, NT, 2, 8, 48, 6, 8><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+  }
   if (rb == 5) {
     k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
     return (int)cudaGetLastError();
@@ -2901,6 +2924,9 @@ int prepare_kernels() {
   BT_SET((k_flux_faces<float, 256, 2>));
   BT_SET((k_flux_faces<float, 512>));
   BT_SET((k_flux_faces<float, 512, 5>));
+  BT_SET((k_flux_faces<float, 512, 5, 20, 128, 16, 8>));
+  BT_SET((k_flux_faces<float, 256, 4, 12, 80, 8, 10>));
+  BT_SET((k_flux_faces<float, 256, 2, 8, 48, 6, 8>));
   BT_SET((k_flux_faces<double, 256>));
   BT_SET((k_flux_faces<double, 256, 5>));
   BT_SET((k_flux_faces<double, 512>));
