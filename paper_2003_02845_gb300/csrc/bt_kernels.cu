@@ -2050,9 +2050,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT >= 512 ? 2 : 1024 / N
     k_flux_faces(Tables tb, State st, double dt, T* dep, DepRec* rec) {
   flux_body<T, NT, 1, RB, NEC, NAC, NMUC, NPHC>(tb, st, dt, dep, rec);
 }
-template <typename T>
+template <typename T, int NEC = 0, int NAC = 0, int NMUC = 0, int NPHC = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_zone_collide(Tables tb, State st, double dt, T* dep, DepRec* rec) {
-  flux_body<T, 256, 2>(tb, st, dt, dep, rec);
+  flux_body<T, 256, 2, default_rb(256), NEC, NAC, NMUC, NPHC>(tb, st, dt, dep, rec);
 }
 
 // ---------------------------------------------------------------------------
@@ -2848,7 +2848,25 @@ int launch_zone_t(const Tables& tb, const State& st, double dt, void* dep, void*
   size_t sm2 = flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 256 / 32, 2, default_rb(256), nullptr, nullptr);
   const int grid = st.zlist ? st.n_zlist : tb.n_zone;
   if (grid <= 0) return 0;
-  k_zone_collide<T><<<grid, 256, sm2, s>>>(tb, st, dt, reinterpret_cast<T*>(dep), reinterpret_cast<DepRec*>(rec));
+  T* d = reinterpret_cast<T*>(dep);
+  DepRec* r = reinterpret_cast<DepRec*>(rec);
+  if constexpr (sizeof(T) == 4) {
+    // two of the benchmark configurations' grids at compile time (as the
+    // face pass; for 20 groups x 128 angles the specialised zone pass spills
+    // and was slower, 19.1 -> 19.3 ms)
+    auto grid_is = [&](int ne, int na, int nmu, int nph) {
+      return tb.n_e == ne && tb.n_ang == na && tb.n_mu == nmu && tb.n_ph == nph;
+    };
+    if (grid_is(12, 80, 8, 10)) {
+      k_zone_collide<T, 12, 80, 8, 10><<<grid, 256, sm2, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+    if (grid_is(8, 48, 6, 8)) {
+      k_zone_collide<T, 8, 48, 6, 8><<<grid, 256, sm2, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+  }
+  k_zone_collide<T><<<grid, 256, sm2, s>>>(tb, st, dt, d, r);
   return (int)cudaGetLastError();
 }
 
@@ -2932,6 +2950,8 @@ int prepare_kernels() {
   BT_SET((k_flux_faces<double, 512>));
   BT_SET((k_flux_faces<double, 512, 5>));
   BT_SET((k_zone_collide<float>));
+  BT_SET((k_zone_collide<float, 12, 80, 8, 10>));
+  BT_SET((k_zone_collide<float, 8, 48, 6, 8>));
   BT_SET((k_zone_collide<double>));
   BT_SET((k_time_remap<float, 128>));
   BT_SET((k_time_remap<float, 256>));

@@ -93,3 +93,24 @@ def test_autotune_considers_split(gpu, tmp_path, monkeypatch):
     nt = t.autotune(0.01)
     assert nt in (128, 256, 512, SPLIT | 256, SPLIT | 512)
     t.step(0.01)   # the chosen shape runs
+
+
+# The face pass has instantiations for the benchmark configurations' grids
+# (groups, mu cells and Phi cells fixed at compile time, float32).  On small
+# spatial grids with those momentum grids, the specialised face pass must
+# give bit for bit what the generic fused kernel gives.
+@pytest.mark.parametrize("n_e,n_mu,n_phi,shape", [(20, 16, 8, SPLIT | 512), (12, 8, 10, SPLIT | 256),
+                                                  (8, 6, 8, SPLIT | 256)])
+def test_specialised_grids_equal_fused(gpu, n_e, n_mu, n_phi, shape):
+    # opacities scaled down: the fluxes and remaps, not the collision, decide f
+    p = W.cc2d(12, 6, n_e, n_mu, n_phi, (1.0, 0.2), W.BASE_SEED + 90 + n_e, "spec_%d_%d_%d" % (n_e, n_mu, n_phi),
+               opacity_scale=1e-4)
+    t = gpu.Transport(p, "mixed")
+    t.set_background(p.backgrounds[0])
+    dt = t.max_dt(0.5)
+    del t
+    a = _run(gpu, p, "mixed", 256, 4, dt)
+    b = _run(gpu, p, "mixed", shape, 4, dt)
+    assert np.array_equal(a.get_f(), b.get_f())
+    for x, y in zip(a.moments(), b.moments()):
+        assert np.array_equal(x, y)
