@@ -2081,8 +2081,22 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, int nt, 
   BT_TAKE(bar, unsigned long long, 2);
   BT_TAKE(src[0], T, (size_t)ne * nang);
   BT_TAKE(src[1], T, (size_t)ne * nang);
-  BT_TAKE(E, T, chunk_elems(ne, nang, nt, 4));   // the energy pass's output (chunk layout)
-  BT_TAKE(dst, T, (size_t)ne * nang);
+  {
+    // the energy pass's output (chunk layout), over the weights and list
+    // bitmasks, which are dead once the lists are built (a species' remapped
+    // rows go back into its own source buffer: no third row buffer)
+    o = (o + 15) & ~size_t(15);
+    const size_t e_bytes = sizeof(T) * chunk_elems(ne, nang, nt, 4);
+    const size_t w_bytes = (sizeof(Wt<T>) * (size_t)nang + 15) & ~size_t(15);
+    const size_t m_bytes = sizeof(unsigned) * (size_t)nang * ((nang + 31) / 32);
+    if (s) {
+      s->E = reinterpret_cast<T*>(base + o);
+      s->W = reinterpret_cast<Wt<T>*>(base + o);
+      s->msk = reinterpret_cast<unsigned*>(base + o + w_bytes);
+      s->dst = nullptr;
+    }
+    o += e_bytes > w_bytes + m_bytes ? e_bytes : w_bytes + m_bytes;
+  }
   BT_TAKE(mu, T, nmu);
   BT_TAKE(n0, T, nang);
   BT_TAKE(n1, T, nang);
@@ -2090,11 +2104,9 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, int nt, 
   BT_TAKE(dOm, T, nang);
   BT_TAKE(dGam, T, ne);
   BT_TAKE(p3, T, 2 * ne + 3);
-  BT_TAKE(W, Wt<T>, nang);
   BT_TAKE(ent.w, T, 4 * nang);
   BT_TAKE(ent.b, short, 4 * nang);
   BT_TAKE(off, short, nang + 1);
-  BT_TAKE(msk, unsigned, (size_t)nang * ((nang + 31) / 32));
   BT_TAKE(redf, ff, 4 * kWarps);     // [species parity][input, output total][warp]
   BT_TAKE(rkey, float, 2 * kWarps);  // [species parity][warp]
   BT_TAKE(ridx, int, 2 * kWarps);
@@ -2146,15 +2158,17 @@ __device__ void remap_correct(const Tables& tb, int nw, const ff* pin, const flo
 // column, the angular pass other columns.  The mixed path's exact-total
 // correction of a species is made by one thread after the next barrier
 // (every thread writes its bins first, uncorrected).
-template <typename T, int NT>
+// NEC, NAC, NMUC, NPHC: the grid's group and angle counts at compile time (0: taken from tb)
+template <typename T, int NT, int NEC = 0, int NAC = 0, int NMUC = 0, int NPHC = 0>
 __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) k_time_remap(Tables tb, State st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RemapSmem<T> S;
-  remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, NT, &S, smem_raw);
-  const int rpt = chunk_rpt(tb.n_e, tb.n_ang, NT, 4);
+  const int NE = NEC ? NEC : tb.n_e, NA = NAC ? NAC : tb.n_ang, NS = tb.n_s;
+  const int NPH = NPHC ? NPHC : tb.n_ph, NMU = NMUC ? NMUC : tb.n_mu;
+  remap_smem_layout<T>(NE, NA, NMU, NT, &S, smem_raw);
+  const int rpt = chunk_rpt(NE, NA, NT, 4);
   constexpr int NW = NT / 32;
   const int zone = blockIdx.x;
-  const int NE = tb.n_e, NA = tb.n_ang, NPH = tb.n_ph, NMU = tb.n_mu, NS = tb.n_s;
   const int nbin = NE * NA;
   const int tid = threadIdx.x;
   const int nch = NT / NA > 0 ? NT / NA : 1;
@@ -2231,21 +2245,15 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) k_time_remap(Tables tb,
     ff* pin = S.redf + (s & 1) * 2 * kWarps;      // [0, kWarps): input total, then output total
     float* pk = S.rkey + (s & 1) * kWarps;
     int* pi = S.ridx + (s & 1) * kWarps;
+    S.dst = src;   // this species' remapped rows, once the energy pass has read src
     if (use_tma) {
-      // the next species' row into the other buffer (free since the last
-      // species' energy pass, two barriers ago)
       unsigned long long* bar_cur = S.bar + (odd ? 1 : 0);
-      unsigned long long* bar_nxt = S.bar + (odd ? 0 : 1);
-      if (tid == 0 && s + 1 < NS) {
-        fence_proxy_async();
-        mbar_expect_tx(bar_nxt, rowbytes);
-        tma_load_1d(odd ? S.src[0] : S.src[1], row(s + 1), rowbytes, bar_nxt);
-      }
       bool ok = mbar_wait(bar_cur, odd ? ph1 : ph0, st.flag);
       if (odd) ph1 ^= 1u; else ph0 ^= 1u;
       if (__syncthreads_or(!ok)) {
-        // give a copy still in flight a bounded chance to land, then stop
-        if (tid == 0 && s + 1 < NS) mbar_wait(bar_nxt, odd ? ph0 : ph1, st.flag);
+        // give the copy in flight a second bounded chance to land, then stop
+        // (the next species' copy is issued only after this one's energy pass)
+        if (tid == 0) mbar_wait(bar_cur, odd ? (ph1 ^ 1u) : (ph0 ^ 1u), st.flag);
         __syncthreads();
         return;
       }
@@ -2270,12 +2278,20 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) k_time_remap(Tables tb,
     // the last species' exact-total correction (its bins were all written
     // before the barrier), by one thread while the others go on
     if (sizeof(T) == 4 && s > 0 && warp == 0) {
-      const int sp = s - 1;
+      const int sp = s - 1;   // its remapped rows are in its own source buffer
       remap_correct<T>(tb, NW, S.redf + (sp & 1) * 2 * kWarps, S.rkey + (sp & 1) * kWarps, S.ridx + (sp & 1) * kWarps,
-                       S.dst, row(sp), Y, c6y, S.n0, S.n1, S.n2, S.dOm);
+                       (sp & 1) ? S.src[1] : S.src[0], row(sp), Y, c6y, S.n0, S.n1, S.n2, S.dOm);
     }
     if (gact) energy_column<T, T>(gc, nch, NE, NA, gb, em, ew, src, S.E, rpt, T(1), P3);
     __syncthreads();
+    // the next species' row into the other buffer: its last readers (the
+    // previous species' output loop and correction) are done
+    if (use_tma && tid == 0 && s + 1 < NS) {
+      unsigned long long* bar_nxt = S.bar + (odd ? 0 : 1);
+      fence_proxy_async();
+      mbar_expect_tx(bar_nxt, rowbytes);
+      tma_load_1d(odd ? S.src[0] : S.src[1], row(s + 1), rowbytes, bar_nxt);
+    }
     // the remapped rows (this thread's own bins), with the mixed path's
     // partials of the output total and of the largest bin
     if (gact) angular_rows<T, T, 4>(gc, nch, NE, NA, rpt, S.off[gb], S.off[gb + 1], S.ent, S.E, StoreT<T>{S.dst, NA, gb});
@@ -2315,7 +2331,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) k_time_remap(Tables tb,
     if (warp == 0) {
       const int sp = NS - 1;
       remap_correct<T>(tb, NW, S.redf + (sp & 1) * 2 * kWarps, S.rkey + (sp & 1) * kWarps, S.ridx + (sp & 1) * kWarps,
-                       S.dst, row(sp), Y, c6y, S.n0, S.n1, S.n2, S.dOm);
+                       (sp & 1) ? S.src[1] : S.src[0], row(sp), Y, c6y, S.n0, S.n1, S.n2, S.dOm);
     }
   }
 }
@@ -2889,9 +2905,27 @@ template <typename T>
 int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
   // 128 threads per CTA (eight CTAs per SM) while one thread per angle
   // fits, else 256: more zones in flight hide the per-zone barriers
+  const size_t sm128 = remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, 128, nullptr, nullptr);
+  if constexpr (sizeof(T) == 4) {
+    // the benchmark configurations' grids at compile time (as the face pass)
+    auto grid_is = [&](int ne, int na, int nmu, int nph) {
+      return tb.n_e == ne && tb.n_ang == na && tb.n_mu == nmu && tb.n_ph == nph;
+    };
+    if (grid_is(20, 128, 16, 8)) {
+      k_time_remap<T, 128, 20, 128, 16, 8><<<tb.n_zone, 128, sm128, s>>>(tb, st);
+      return (int)cudaGetLastError();
+    }
+    if (grid_is(12, 80, 8, 10)) {
+      k_time_remap<T, 128, 12, 80, 8, 10><<<tb.n_zone, 128, sm128, s>>>(tb, st);
+      return (int)cudaGetLastError();
+    }
+    if (grid_is(8, 48, 6, 8)) {
+      k_time_remap<T, 128, 8, 48, 6, 8><<<tb.n_zone, 128, sm128, s>>>(tb, st);
+      return (int)cudaGetLastError();
+    }
+  }
   if (tb.n_ang <= 128)
-    k_time_remap<T, 128><<<tb.n_zone, 128, remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, 128, nullptr, nullptr), s>>>(
-        tb, st);
+    k_time_remap<T, 128><<<tb.n_zone, 128, sm128, s>>>(tb, st);
   else
     k_time_remap<T, 256><<<tb.n_zone, 256, remap_smem_layout<T>(tb.n_e, tb.n_ang, tb.n_mu, 256, nullptr, nullptr), s>>>(
         tb, st);
@@ -2954,6 +2988,9 @@ int prepare_kernels() {
   BT_SET((k_zone_collide<float, 8, 48, 6, 8>));
   BT_SET((k_zone_collide<double>));
   BT_SET((k_time_remap<float, 128>));
+  BT_SET((k_time_remap<float, 128, 20, 128, 16, 8>));
+  BT_SET((k_time_remap<float, 128, 12, 80, 8, 10>));
+  BT_SET((k_time_remap<float, 128, 8, 48, 6, 8>));
   BT_SET((k_time_remap<float, 256>));
   BT_SET((k_time_remap<double, 128>));
   BT_SET((k_time_remap<double, 256>));
