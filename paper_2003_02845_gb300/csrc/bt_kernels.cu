@@ -653,6 +653,7 @@ __device__ __forceinline__ void angular_block(int t0, int nch, int ne, const T* 
   A acc[RB];
 #pragma unroll
   for (int j = 0; j < RB; ++j) acc[j] = A(0);
+#pragma unroll 2
   for (int k = 0; k < nmax; ++k) {
     if (k < n) {
       const A w = (A)ent.w[e0 + k];
