@@ -285,8 +285,9 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   return fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
 }
 // 1/d by one Newton step from the float reciprocal: x + x (1 - d x)
+// (__frcp_rn: the correctly rounded reciprocal, the value of 1.0f / d.hi)
 __device__ __forceinline__ ff ff_recip(ff d) {
-  float x = 1.0f / d.hi;
+  float x = __frcp_rn(d.hi);
   ff e = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul_f(d, x)));
   return ff_add(ff{x, 0.0f}, ff_mul_f(e, x));
 }
@@ -1933,7 +1934,8 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       }
       const ff J = ff_mul(sr, ff_recip(s1));
       const ff ksJ = ff_mul(ks_f, J);
-      float fN = 0.0f, fE = 0.0f, fP0 = 0.0f, fP1 = 0.0f, fP2 = 0.0f;
+      // number and momentum weights of the row; energy is eps_i times them
+      float fN = 0.0f, fP0 = 0.0f, fP1 = 0.0f, fP2 = 0.0f;
       const float eps_i = (float)S.epsS[i];
       const float dg_i = (float)S.dGam[i];
       for (int ang = lane; ang < NA; ang += 32) {
@@ -1948,24 +1950,21 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         const ff del = ff_add(ff{fw, 0.0f}, ff_neg(fst));
         const float dc = S.zq_f[ang] * dg_i * (del.hi + del.lo);
         fN += dc;
-        const float de = dc * eps_i;
-        fE += de;
-        fP0 += de * (float)S.n0[ang];
-        fP1 += de * (float)S.n1[ang];
-        fP2 += de * (float)S.n2[ang];
+        fP0 += dc * (float)S.n0[ang];
+        fP1 += dc * (float)S.n1[ang];
+        fP2 += dc * (float)S.n2[ang];
       }
       // the lane sums are float32 already: reduce them in float32 too
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         fN += __shfl_xor_sync(0xffffffffu, fN, o);
-        fE += __shfl_xor_sync(0xffffffffu, fE, o);
         fP0 += __shfl_xor_sync(0xffffffffu, fP0, o);
         fP1 += __shfl_xor_sync(0xffffffffu, fP1, o);
         fP2 += __shfl_xor_sync(0xffffffffu, fP2, o);
       }
       if (lane == 0) {   // float32 row partials; summed per species below
         float* zf = reinterpret_cast<float*>(S.zrow) + (size_t)row * 5;
-        zf[0] = fN; zf[1] = fE; zf[2] = fP0; zf[3] = fP1; zf[4] = fP2;
+        zf[0] = fN; zf[1] = fN * eps_i; zf[2] = fP0 * eps_i; zf[3] = fP1 * eps_i; zf[4] = fP2 * eps_i;
       }
     }
     if constexpr (sizeof(T) == 8) {
