@@ -249,14 +249,16 @@ int bt_peak_fma(int precision, double* flops_per_s, void* stream);
  * kernel in which each zone's CTA computes all of its faces (every interior
  * face is computed by both neighbours) and then its collision solve, with
  * that many threads per CTA (default 256, or the choice cached by the
- * autotuner).  BT_SHAPE_SPLIT | 256 or | 512: the split form, a face pass in
+ * autotuner).  BT_SHAPE_SPLIT | 256, | 384 or | 512: the split form, a face pass in
  * which every face is computed once (by the zone that owns it) and writes both
  * neighbours' deposits, then a zone pass that gathers a zone's deposits in
  * the fused order and solves its collision; it needs 6 x the f array in
  * deposit rows, allocated when the shape is set.  A shape needs at least one
  * thread per angle bin (threads >= n_mu * n_phi); one that does not fit the
  * problem (threads, shared memory, registers) is refused with BT_ERR_ARG and
- * is not tried by the autotuner.  FP64 results are bitwise the same for
+ * is not tried by the autotuner (BT_SHAPE_SPLIT | 384 exists in the mixed
+ * precision only: three 128-angle chunks of a 20-group row, for example, at
+ * two CTAs per SM without spilling registers).  FP64 results are bitwise the same for
  * every shape; mixed-precision results agree to float32 rounding (their
  * exact-total sums are formed in a shape-dependent order). */
 #define BT_SHAPE_SPLIT 0x10000

@@ -416,7 +416,8 @@ static void release_split(bt_handle* h) {
   h->dep = h->rec = nullptr;
 }
 static bool valid_shape(int nt) {
-  return nt == 128 || nt == 256 || nt == 512 || nt == (bt::kShapeSplit | 256) || nt == (bt::kShapeSplit | 512);
+  return nt == 128 || nt == 256 || nt == 512 || nt == (bt::kShapeSplit | 256) || nt == (bt::kShapeSplit | 384) ||
+         nt == (bt::kShapeSplit | 512);
 }
 static bool shape_fits(const bt_handle* h, int nt) {
   // the flux kernels give each angle of a row its own thread (a CTA of fewer
@@ -1005,7 +1006,7 @@ int bt_autotune(bt_handle* h, double dt, int* chosen_nt) {
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(BT_ERR_DT, "dt must be positive and finite");
   bind_state(h);
   const int S = bt::kShapeSplit;
-  const int cand[5] = {128, 256, 512, S | 256, S | 512};
+  const int cand[6] = {128, 256, 512, S | 256, S | 384, S | 512};
   float best = 0.f;
   int best_nt = h->nt;
   // the trial launches write the per-zone moments and outflow of a step that
@@ -1079,7 +1080,7 @@ int bt_launch_shape(const bt_handle* h, int* threads_per_cta) {
 int bt_set_launch_shape(bt_handle* h, int threads_per_cta) {
   if (!h) return fail(BT_ERR_ARG, "NULL");
   if (!valid_shape(threads_per_cta))
-    return fail(BT_ERR_ARG, "launch shape must be 128, 256, 512, BT_SHAPE_SPLIT | 256 or BT_SHAPE_SPLIT | 512");
+    return fail(BT_ERR_ARG, "launch shape must be 128, 256, 512, or BT_SHAPE_SPLIT | 256, 384 or 512");
   if (!shape_fits(h, threads_per_cta)) return fail(BT_ERR_ARG, "launch shape does not fit this problem");
   if (threads_per_cta & bt::kShapeSplit) {
     int rc = ensure_split(h);

@@ -101,7 +101,7 @@ struct LaunchCfg {
 // cudaError_t as int.
 int launch_time_remap(const Tables& T, const State& S, int mixed, void* stream);
 // launch shape nt: threads per CTA (128, 256, 512), or kShapeSplit | threads
-// (256, 512) for the split form, whose face pass launch_flux_collide then
+// (256, 512; 384 in float32 only) for the split form, whose face pass launch_flux_collide then
 // launches (the zone pass is launch_zone_collide); it needs the deposit
 // buffers dep (split_dep_bytes) and rec (split_rec_bytes)
 constexpr int kShapeSplit = 0x10000;

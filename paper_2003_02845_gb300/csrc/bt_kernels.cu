@@ -2808,6 +2808,11 @@ template <typename T, int NT>
 int face_rb(const Tables& tb) {
   const int nch = chunk_nch(tb.n_ang, NT);
   const int rows = (tb.n_e + nch - 1) / nch;
+  if (NT == 384) {
+    // the 384-thread face pass (float32 only): seven rows a walk on 20
+    // groups x 128 angles (three chunks), else blocks of four
+    return (tb.n_e == 20 && tb.n_ang == 128 && tb.n_mu == 16 && tb.n_ph == 8) ? 7 : 4;
+  }
   if (rows % 5 == 0) return 5;
   if (sizeof(T) == 4 && NT < 512 && rows <= 2) return 2;
   return default_rb(NT);
@@ -2830,6 +2835,12 @@ int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void
   auto grid_is = [&](int ne, int na, int nmu, int nph) {
     return tb.n_e == ne && tb.n_ang == na && tb.n_mu == nmu && tb.n_ph == nph;
   };
+  if constexpr (sizeof(T) == 4 && NT == 384) {
+    if (rb == 7 && grid_is(20, 128, 16, 8)) {
+      k_flux_faces<T, NT, 7, 20, 128, 16, 8><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
+  }
   if constexpr (sizeof(T) == 4 && NT == 512) {
     if (rb == 5 && grid_is(20, 128, 16, 8)) {
       k_flux_faces<T, NT, 5, 20, 128, 16, 8><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
@@ -2846,9 +2857,11 @@ int launch_faces_t(const Tables& tb, const State& st, double dt, void* dep, void
       return (int)cudaGetLastError();
     }
   }
-  if (rb == 5) {
-    k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
-    return (int)cudaGetLastError();
+  if constexpr (NT != 384) {
+    if (rb == 5) {
+      k_flux_faces<T, NT, 5><<<grid, NT, sm1, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
   }
   if constexpr (sizeof(T) == 4 && NT == 256) {
     if (rb == 2) {
@@ -2937,8 +2950,9 @@ int launch_remap_t(const Tables& tb, const State& st, cudaStream_t s) {
 size_t flux_smem_bytes(const Tables& tb, int mixed, int nt) {
   const int threads = nt & 0xFFFF;
   if (nt & kShapeSplit) {
-    size_t a = threads >= 512 ? (mixed ? faces_smem<float, 512>(tb) : faces_smem<double, 512>(tb))
-                              : (mixed ? faces_smem<float, 256>(tb) : faces_smem<double, 256>(tb));
+    size_t a = threads >= 512   ? (mixed ? faces_smem<float, 512>(tb) : faces_smem<double, 512>(tb))
+               : threads == 384 ? faces_smem<float, 384>(tb)   // (float32 only; not offered in float64)
+                                : (mixed ? faces_smem<float, 256>(tb) : faces_smem<double, 256>(tb));
     size_t b = mixed ? flux_smem_layout<float>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, 4, nullptr, nullptr)
                      : flux_smem_layout<double>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, 8, 2, 4, nullptr, nullptr);
     return a > b ? a : b;
@@ -2977,6 +2991,8 @@ int prepare_kernels() {
   BT_SET((k_flux_faces<float, 512>));
   BT_SET((k_flux_faces<float, 512, 5>));
   BT_SET((k_flux_faces<float, 512, 5, 20, 128, 16, 8>));
+  BT_SET((k_flux_faces<float, 384>));
+  BT_SET((k_flux_faces<float, 384, 7, 20, 128, 16, 8>));
   BT_SET((k_flux_faces<float, 256, 4, 12, 80, 8, 10>));
   BT_SET((k_flux_faces<float, 256, 2, 8, 48, 6, 8>));
   BT_SET((k_flux_faces<double, 256>));
@@ -3004,6 +3020,7 @@ int flux_occupancy(const Tables& tb, int mixed, int nt) {
     switch (nt & 0xFFFF) {
       case 256: return mixed ? split_occupancy_t<float, 256>(tb) : split_occupancy_t<double, 256>(tb);
       case 512: return mixed ? split_occupancy_t<float, 512>(tb) : split_occupancy_t<double, 512>(tb);
+      case 384: return mixed ? split_occupancy_t<float, 384>(tb) : 0;   // float32 only
       default: return 0;
     }
   }
@@ -3028,6 +3045,8 @@ int launch_flux_collide(const Tables& tb, const State& st, double dt, int mixed,
     if (!dep || !rec) return (int)cudaErrorInvalidValue;
     if ((nt & 0xFFFF) == 512)
       return mixed ? launch_faces_t<float, 512>(tb, st, dt, dep, rec, s) : launch_faces_t<double, 512>(tb, st, dt, dep, rec, s);
+    if ((nt & 0xFFFF) == 384)
+      return mixed ? launch_faces_t<float, 384>(tb, st, dt, dep, rec, s) : (int)cudaErrorInvalidValue;
     return mixed ? launch_faces_t<float, 256>(tb, st, dt, dep, rec, s) : launch_faces_t<double, 256>(tb, st, dt, dep, rec, s);
   }
   switch (nt) {

@@ -67,7 +67,9 @@ def _run(gpu, p, precision, shape, steps, dt):
 def test_split_equals_fused(gpu, case, precision):
     p = _cases()[case]
     a = _run(gpu, p, precision, 256, 6, 0.004)
-    for shape in (SPLIT | 256, SPLIT | 512):
+    # (the 384-thread face pass exists in the mixed precision only)
+    shapes = (SPLIT | 256, SPLIT | 512) if precision == "fp64" else (SPLIT | 256, SPLIT | 384, SPLIT | 512)
+    for shape in shapes:
         b = _run(gpu, p, precision, shape, 6, 0.004)
         assert np.array_equal(a.get_f(), b.get_f())
         for x, y in zip(a.moments(), b.moments()):
@@ -99,8 +101,8 @@ def test_autotune_considers_split(gpu, tmp_path, monkeypatch):
 # (groups, mu cells and Phi cells fixed at compile time, float32).  On small
 # spatial grids with those momentum grids, the specialised face pass must
 # give bit for bit what the generic fused kernel gives.
-@pytest.mark.parametrize("n_e,n_mu,n_phi,shape", [(20, 16, 8, SPLIT | 512), (12, 8, 10, SPLIT | 256),
-                                                  (8, 6, 8, SPLIT | 256)])
+@pytest.mark.parametrize("n_e,n_mu,n_phi,shape", [(20, 16, 8, SPLIT | 512), (20, 16, 8, SPLIT | 384),
+                                                  (12, 8, 10, SPLIT | 256), (8, 6, 8, SPLIT | 256)])
 def test_specialised_grids_equal_fused(gpu, n_e, n_mu, n_phi, shape):
     # opacities scaled down: the fluxes and remaps, not the collision, decide f
     p = W.cc2d(12, 6, n_e, n_mu, n_phi, (1.0, 0.2), W.BASE_SEED + 90 + n_e, "spec_%d_%d_%d" % (n_e, n_mu, n_phi),
@@ -114,3 +116,10 @@ def test_specialised_grids_equal_fused(gpu, n_e, n_mu, n_phi, shape):
     assert np.array_equal(a.get_f(), b.get_f())
     for x, y in zip(a.moments(), b.moments()):
         assert np.array_equal(x, y)
+
+
+def test_split_384_is_mixed_only(gpu):
+    p = W.cc2d(8, 4, 20, 16, 8, (1.0,), W.BASE_SEED + 95, "spec_fp64_384")
+    t = gpu.Transport(p, "fp64")
+    with pytest.raises(gpu.BtError):
+        t.set_launch_shape(SPLIT | 384)
