@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([NVCC, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"])
+    subprocess.check_call([NVCC, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

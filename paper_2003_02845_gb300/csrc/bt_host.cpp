@@ -8,12 +8,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cfloat>
 #include <cstring>
 #include <fstream>
 #include <map>
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bt.h"
@@ -164,6 +166,36 @@ double volume(double r0, double r1, double th0, double th1, double dph) {
 bool finite_all(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// Every value of p[0..n) in [lo, hi] (a NaN fails both comparisons).  The
+// backgrounds of large problems are hundreds of MB per call, so the check is
+// branch-free within blocks (the compiler vectorises it) and large arrays are
+// split over a few host threads.
+static bool block_in(const double* p, size_t n, double lo, double hi) {
+  for (size_t i = 0; i < n;) {
+    const size_t e = std::min(n, i + 4096);
+    int ok = 1;
+    for (; i < e; ++i) ok &= (p[i] >= lo) & (p[i] <= hi);
+    if (!ok) return false;
+  }
+  return true;
+}
+static bool all_in(const double* p, size_t n, double lo, double hi) {
+  const size_t per = size_t(1) << 21;   // elements a thread takes at least
+  const size_t nt = std::min<size_t>(8, n / per);
+  if (nt < 2) return block_in(p, n, lo, hi);
+  std::vector<char> ok(nt, 1);
+  std::vector<std::thread> th;
+  const size_t chunk = (n + nt - 1) / nt;
+  for (size_t t = 0; t < nt; ++t) {
+    const size_t a = t * chunk, b = std::min(n, a + chunk);
+    th.emplace_back([&, t, a, b] { ok[t] = block_in(p + a, b - a, lo, hi) ? 1 : 0; });
+  }
+  for (auto& x : th) x.join();
+  for (char c : ok)
+    if (!c) return false;
   return true;
 }
 
@@ -707,9 +739,15 @@ int bt_set_background(bt_handle* h, int mem, const double* rho, const double* T,
   if (mem != BT_MEM_HOST && mem != BT_MEM_DEVICE) return fail(BT_ERR_ARG, "mem");
   const size_t nz = h->nzone, no = (size_t)h->cfg.n_species * nz * h->cfg.n_eps;
   if (mem == BT_MEM_HOST) {
-    if (!finite_all(v, 3 * nz) || !finite_all(alpha, nz) || !finite_all(phi, nz) || !finite_all(kappa_a, no) ||
-        !finite_all(kappa_s, no) || !finite_all(f_eq, no))
+    if (!finite_all(v, 3 * nz) || !finite_all(alpha, nz) || !finite_all(phi, nz) ||
+        !all_in(f_eq, no, -DBL_MAX, DBL_MAX))
       return fail(BT_ERR_BACKGROUND, "non-finite background value");
+    // opacities: finite and non-negative, in one pass
+    if (!all_in(kappa_a, no, 0.0, DBL_MAX) || !all_in(kappa_s, no, 0.0, DBL_MAX)) {
+      if (!finite_all(kappa_a, no) || !finite_all(kappa_s, no))
+        return fail(BT_ERR_BACKGROUND, "non-finite background value");
+      return fail(BT_ERR_BACKGROUND, "negative opacity");
+    }
     for (size_t z = 0; z < nz; ++z) {
       if (!(alpha[z] > 0.0) || !(phi[z] > 0.0)) return fail(BT_ERR_BACKGROUND, "alpha and phi must be > 0");
       double v2 = v[3 * z] * v[3 * z] + v[3 * z + 1] * v[3 * z + 1] + v[3 * z + 2] * v[3 * z + 2];
@@ -717,8 +755,6 @@ int bt_set_background(bt_handle* h, int mem, const double* rho, const double* T,
       if (shift && (shift[3 * z] != 0.0 || shift[3 * z + 1] != 0.0 || shift[3 * z + 2] != 0.0))
         return fail(BT_ERR_BACKGROUND, "non-zero shift is not supported");
     }
-    for (size_t q = 0; q < no; ++q)
-      if (kappa_a[q] < 0.0 || kappa_s[q] < 0.0) return fail(BT_ERR_BACKGROUND, "negative opacity");
   }
   int nxt = h->has_bg ? 1 - h->cur : h->cur;
   int rc;

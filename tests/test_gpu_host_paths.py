@@ -2,6 +2,8 @@
 the oracle, the batch graph cache after the buffers it captured were freed
 and replaced, the autotuner leaving the last step's moments alone, and the
 choice of a launch shape at creation when the fused form does not fit."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -99,3 +101,23 @@ def test_create_picks_a_shape_that_fits(orc, gpu):
         t.set_background(p.backgrounds[(k + 1) % 2])
         t.step(dt)
     assert rel_l1(t.get_f(), o.get_f()) <= 1e-4
+
+
+def test_background_checks(gpu):
+    # host backgrounds are checked before anything is copied: a NaN or a
+    # negative opacity is refused (BT_ERR_BACKGROUND); the opacities here are
+    # large enough (4 species x 65536 zones x 20 groups) for the check to be
+    # split over host threads
+    p = W.cc2d(512, 128, 20, 2, 2, (1.0, 0.5, 0.2, 0.2), W.BASE_SEED + 97, "checks")
+    t = gpu.Transport(p, "mixed")
+    t.set_background(p.backgrounds[0])
+    for field, idx, val in (("kappa_a", (3, 60000, 19), -1.0), ("kappa_s", (2, 123, 4), float("nan")),
+                            ("f_eq", (1, 65535, 0), float("inf"))):
+        bad = copy.deepcopy(p.backgrounds[1])
+        getattr(bad, field)[idx] = val
+        with pytest.raises(gpu.BtError) as e:
+            t.set_background(bad)
+        assert e.value.code == -2
+    t.set_background(p.backgrounds[1])   # a valid one is still taken
+    t.set_f(p.f0)
+    t.step(t.max_dt(0.5))
