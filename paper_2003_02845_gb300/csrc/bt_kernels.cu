@@ -355,6 +355,13 @@ struct AList {
   short* b;
   __device__ __forceinline__ AList operator+(int o) const { return AList{w + o, b + o}; }
 };
+// Entry e of a remap's lists is stored at alist_at(e): one word of padding
+// after every 32 entries.  The lanes of a warp read their lists about four
+// entries apart, so without it lanes eight apart would hit one bank.
+__host__ __device__ __forceinline__ int alist_at(int e) { return e + (e >> 5); }
+// entries of one remap's block: 4 na entries (four targets per source angle)
+// with their padding
+__host__ __device__ __forceinline__ int alist_block(int na) { return alist_at(4 * na) + 1; }
 
 // the angular targets of one source angle in four fixed slots (mu bracket
 // lower/upper x Phi bracket lower/upper); a slot whose weight is zero, or
@@ -382,7 +389,8 @@ __device__ __forceinline__ void ang_targets4(const Wt<T>& W, int nmu, int nph, i
 // does not depend on the order), the offsets are a scan of the masks' bit
 // counts, and an entry's place in its list is the number of lower sources in
 // the mask: no sorting pass, and all threads take part.
-// off: [nr][na+1], msk: [nr][na][ceil(na/32)] scratch, ent: [nr][4 na].
+// off: [nr][na+1], msk: [nr][na][ceil(na/32)] scratch, ent: [nr][alist_block(na)]
+// (entry e of a remap's lists at alist_at(e)).
 // Whole block (synchronises at the end).
 template <typename T>
 __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int nmu, int nph, short* off,
@@ -439,8 +447,8 @@ __device__ void build_alists(const Wt<T>* W, int nr, unsigned mask, int na, int 
       int pos = off[r * (na + 1) + tgt[k]];
       for (int w = 0; w < (b >> 5); ++w) pos += __popc(mt[w]);
       pos += __popc(mt[b >> 5] & ((1u << (b & 31)) - 1u));
-      ent.w[r * 4 * na + pos] = wa[k];
-      ent.b[r * 4 * na + pos] = (short)b;
+      ent.w[r * alist_block(na) + alist_at(pos)] = wa[k];
+      ent.b[r * alist_block(na) + alist_at(pos)] = (short)b;
     }
   }
   __syncthreads();
@@ -657,8 +665,9 @@ __device__ __forceinline__ void angular_block(int t0, int nch, int ne, const T* 
 #pragma unroll 2
   for (int k = 0; k < nmax; ++k) {
     if (k < n) {
-      const A w = (A)ent.w[e0 + k];
-      const T* eb = Eb + ent.b[e0 + k] * rpt;
+      const int e = alist_at(e0 + k);
+      const A w = (A)ent.w[e];
+      const T* eb = Eb + ent.b[e] * rpt;
 #pragma unroll
       for (int j = 0; j < RB; ++j) acc[j] += w * (A)eb[j];
     }
@@ -941,8 +950,8 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
     }
     o = o_b + tot;
   }
-  BT_TAKE(ent.w, T, mode == 2 ? 0 : 6 * 4 * nang);
-  BT_TAKE(ent.b, short, mode == 2 ? 0 : 6 * 4 * nang);
+  BT_TAKE(ent.w, T, mode == 2 ? 0 : 6 * alist_block(nang));
+  BT_TAKE(ent.b, short, mode == 2 ? 0 : 6 * alist_block(nang));
   BT_TAKE(off, short, mode == 2 ? 0 : 6 * (nang + 1));
   BT_TAKE(n0, T, nang);
   BT_TAKE(n1, T, nang);
@@ -1416,7 +1425,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           const short* off = S.off + slot * (NA + 1);
           // (both outer cells' values go to the first row: each bin reads one)
           StoreG<T> st_g{SRC + k * nbin, csb, NA, gb};
-          angular_rows<T, T, RB>(gc, nch, NE, NA, rpt, off[gb], off[gb + 1], S.ent + slot * 4 * NA, EB + slot * ebs, st_g);
+          angular_rows<T, T, RB>(gc, nch, NE, NA, rpt, off[gb], off[gb + 1], S.ent + slot * alist_block(NA), EB + slot * ebs, st_g);
         }
       }
       __syncthreads();
@@ -1635,7 +1644,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         for (int side = 0; side < 2; ++side) {
           if (!(side == 0 ? depP : depQ)) continue;
           const short* off = S.off + (4 + side) * (NA + 1);
-          const AList<T> ent = S.ent + (4 + side) * 4 * NA;
+          const AList<T> ent = S.ent + (4 + side) * alist_block(NA);
           const T* Es = side == 0 ? EP : EQ;
           const T sgn = side == 0 ? T(-1) : T(1);
           if (MODE == 0) {
@@ -2104,8 +2113,8 @@ __host__ __device__ size_t remap_smem_layout(int ne, int nang, int nmu, int nt, 
   BT_TAKE(dOm, T, nang);
   BT_TAKE(dGam, T, ne);
   BT_TAKE(p3, T, 2 * ne + 3);
-  BT_TAKE(ent.w, T, 4 * nang);
-  BT_TAKE(ent.b, short, 4 * nang);
+  BT_TAKE(ent.w, T, alist_block(nang));
+  BT_TAKE(ent.b, short, alist_block(nang));
   BT_TAKE(off, short, nang + 1);
   BT_TAKE(redf, ff, 4 * kWarps);     // [species parity][input, output total][warp]
   BT_TAKE(rkey, float, 2 * kWarps);  // [species parity][warp]
