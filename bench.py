@@ -176,13 +176,13 @@ def host_cpu():
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (218.26e6 + 1351.15e6 + 1354.69e6 + 480.81e6, "cb3d0b82125e3a248850939001b1d0286839f0791ead313cca6fb3234046c1ef"),
+        (217.38e6 + 1347.32e6 + 1354.82e6 + 476.44e6, "ceecd41ffa5c3e8efbc4c7dc9b455d8cdf0f8503f937a5a8621cab078f73d1e5"),
     # captured on the same problem at 128 x 32 zones (python -m
     # paper_2003_02845_gb300.profiling config5_largest_128x32 mixed split/384 3)
     # and scaled by the 16x zones of the full 512 x 128 grid (the traffic of
     # both passes is per zone)
     ("config5_p2_512x128x20x128x6", "mixed", "split/384"):
-        (16 * (490.88e6 + 1460.63e6 + 2012.19e6 + 503.91e6), "cb3d0b82125e3a248850939001b1d0286839f0791ead313cca6fb3234046c1ef"),
+        (16 * (484.72e6 + 1458.99e6 + 2012.13e6 + 500.31e6), "ceecd41ffa5c3e8efbc4c7dc9b455d8cdf0f8503f937a5a8621cab078f73d1e5"),
 }
 
 
