@@ -916,9 +916,9 @@ __host__ __device__ size_t flux_smem_layout(int ns, int ne, int nang, int nmu, i
   BT_TAKE(red, double, kMaxWarps * 2);
   BT_TAKE(zsc, double, mode == 1 ? 0 : 8);
   BT_TAKE(tally, double, ns * 2);
-  BT_TAKE(corr, double, ns);
-  BT_TAKE(corr_f, ff, ns);
-  BT_TAKE(corr_at, int, ns);
+  BT_TAKE(corr, double, mode == 1 ? 0 : ns);   // the corrections: not in the face pass
+  BT_TAKE(corr_f, ff, mode == 1 ? 0 : ns);
+  BT_TAKE(corr_at, int, mode == 1 ? 0 : ns);
   BT_TAKE(dtot, ff, ns);
   BT_TAKE(redf, ff, kMaxWarps);
   BT_TAKE(redfS, ff, mode == 2 ? (size_t)ns * kMaxWarps : 0);
