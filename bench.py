@@ -176,13 +176,13 @@ def host_cpu():
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (217.38e6 + 1347.32e6 + 1354.82e6 + 476.44e6, "ceecd41ffa5c3e8efbc4c7dc9b455d8cdf0f8503f937a5a8621cab078f73d1e5"),
+        (218.70e6 + 1350.32e6 + 1354.86e6 + 477.39e6, "9086fa4fd14f6483e7b076f35b48b2e40d05d1e2e0784b8eb8cddddf932bbae6"),
     # captured on the same problem at 128 x 32 zones (python -m
     # paper_2003_02845_gb300.profiling config5_largest_128x32 mixed split/384 3)
     # and scaled by the 16x zones of the full 512 x 128 grid (the traffic of
     # both passes is per zone)
     ("config5_p2_512x128x20x128x6", "mixed", "split/384"):
-        (16 * (484.72e6 + 1458.99e6 + 2012.13e6 + 500.31e6), "ceecd41ffa5c3e8efbc4c7dc9b455d8cdf0f8503f937a5a8621cab078f73d1e5"),
+        (16 * (488.12e6 + 1459.07e6 + 2012.18e6 + 500.39e6), "9086fa4fd14f6483e7b076f35b48b2e40d05d1e2e0784b8eb8cddddf932bbae6"),
 }
 
 
