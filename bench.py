@@ -176,13 +176,13 @@ def host_cpu():
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (218.70e6 + 1350.32e6 + 1354.86e6 + 477.39e6, "9086fa4fd14f6483e7b076f35b48b2e40d05d1e2e0784b8eb8cddddf932bbae6"),
+        (218.60e6 + 1347.00e6 + 1352.24e6 + 429.06e6, "e955d870757d1f0a8e91dea04428eac79e240bc965e439bec4f801e18e4a3b74"),
     # captured on the same problem at 128 x 32 zones (python -m
     # paper_2003_02845_gb300.profiling config5_largest_128x32 mixed split/384 3)
     # and scaled by the 16x zones of the full 512 x 128 grid (the traffic of
     # both passes is per zone)
     ("config5_p2_512x128x20x128x6", "mixed", "split/384"):
-        (16 * (488.12e6 + 1459.07e6 + 2012.18e6 + 500.39e6), "9086fa4fd14f6483e7b076f35b48b2e40d05d1e2e0784b8eb8cddddf932bbae6"),
+        (16 * (486.50e6 + 1459.17e6 + 2011.19e6 + 508.88e6), "e955d870757d1f0a8e91dea04428eac79e240bc965e439bec4f801e18e4a3b74"),
 }
 
 

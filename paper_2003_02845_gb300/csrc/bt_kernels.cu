@@ -284,12 +284,15 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   ff p = two_prod(a.hi, b);
   return fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
 }
-// 1/d by one Newton step from the float reciprocal: x + x (1 - d x)
-// (__frcp_rn: the correctly rounded reciprocal, the value of 1.0f / d.hi)
+// 1/d by one Newton step from the float reciprocal: x + x e, e = 1 - d x
+// (__frcp_rn: the correctly rounded reciprocal, the value of 1.0f / d.hi).
+// |e| <= 2^-24, and 1 - d.hi x has at most 24 significant bits, so the inner
+// fused multiply-add forms it exactly; the outer one adds -d.lo x with one
+// rounding (2^-48 absolute).  The result has about 46 correct bits.
 __device__ __forceinline__ ff ff_recip(ff d) {
-  float x = __frcp_rn(d.hi);
-  ff e = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul_f(d, x)));
-  return ff_add(ff{x, 0.0f}, ff_mul_f(e, x));
+  const float x = __frcp_rn(d.hi);
+  const float e = fmaf(-d.lo, x, fmaf(-d.hi, x, 1.0f));
+  return fast_two_sum(x, x * e);
 }
 __device__ __forceinline__ ff ff_from_d(double v) {
   float hi = (float)v;
@@ -1138,6 +1141,9 @@ template <typename T, int NT, int MODE, int RB = default_rb(NT), int NEC = 0, in
 __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, double dt, T* dep, DepRec* rec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using DN = typename DNT<T>::type;
+  // paired loads in the zone pass's gather (registers allow them where the
+  // grid is fixed at compile time)
+  constexpr bool kPair = NEC > 0;
   FluxSmem<T> S;
   flux_smem_layout<T>(tb.n_s, tb.n_e, tb.n_ang, tb.n_mu, NT / 32, MODE, RB, &S, smem_raw);
   const int zone = st.zlist ? st.zlist[blockIdx.x] : (int)blockIdx.x;
@@ -1722,20 +1728,43 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       ff part = ff{0.0f, 0.0f};
       float bk = -1.0f;
       int bi = 0x7fffffff;
-      for (int q = tid; q < nbin; q += NT) {
-        DN acc;
-        if (tb.pole) {
-          acc = dNs[q];
-        } else {
-          acc = gather(base, q);
-          dNs[q] = acc;
-        }
+      auto tally = [&](int q, DN acc) {
         if (sizeof(T) == 4) {
           const float c = (float)acc * (float)S.dGam[q / NA];
           part = ff_add(part, two_prod((float)acc, (float)S.dGam[q / NA]));
           const float k = fabsf(c);
           if (k > bk) { bk = k; bi = q; }
         }
+      };
+      // with the grid fixed at compile time, two elements a thread per pass,
+      // all of their rows loaded before either is summed (twice the loads
+      // in flight; the generic kernel has no registers for them); each
+      // thread still tallies its elements in ascending order
+      for (int q0 = tid; q0 < nbin; q0 += kPair ? 2 * NT : NT) {
+        const int q1 = q0 + NT;
+        const bool has1 = kPair && q1 < nbin;
+        DN acc0, acc1 = DN(0);
+        if (tb.pole) {
+          acc0 = dNs[q0];
+          if (has1) acc1 = dNs[q1];
+        } else {
+          T v0[8], v1[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (k < nrow) {
+              v0[k] = base[(size_t)rows[k] * NS * nbin + q0];
+              v1[k] = has1 ? base[(size_t)rows[k] * NS * nbin + q1] : T(0);
+            }
+          }
+          acc0 = DN(0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (k < nrow) { acc0 += (DN)v0[k]; acc1 += (DN)v1[k]; }
+          dNs[q0] = acc0;
+          if (has1) dNs[q1] = acc1;
+        }
+        tally(q0, acc0);
+        if (has1) tally(q1, acc1);
       }
       if (sizeof(T) == 4) {
         // warp reductions now; the block's, for every species, after one
@@ -1919,30 +1948,46 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
       const ff ka_f = S.rowk[4 * row], ks_f = S.rowk[4 * row + 1];
       const ff kt_f = S.rowk[4 * row + 2], kafe_f = S.rowk[4 * row + 3];
       float* buf = reinterpret_cast<float*>(S.wr_r) + (size_t)warp * 4 * NA;   // fst.hi, fst.lo, iD.hi, iD.lo
-      ff sr = ff{0.0f, 0.0f}, s1 = ff{0.0f, 0.0f};
+      // per bin f* = f + zcn dN and 1/D; per row A = sum dOm f*/D,
+      // B = sum dOm tau/D, C = sum dOm/D, so that sum dOm r/D = A + ka fe B
+      // and sum dOm (1 + ka tau)/D = C + ka B
+      ff sA = ff{0.0f, 0.0f}, sB = ff{0.0f, 0.0f}, sC = ff{0.0f, 0.0f};
       const ff cval_f = S.corr_f[s];
-      for (int ang = lane; ang < NA; ang += 32) {
+      auto bin1 = [&](int ang, float dnv, float fzv) {
         const ff tau = S.zt_f[ang];
         const ff zcn = S.zc_f[ang];
         const ff dom = S.zd_f[ang];
-        ff dnv = ff{(float)dn[ang], 0.0f};
-        if (ang == cat) dnv = ff_add(dnv, cval_f);
-        const ff fst = ff_add(ff{(float)fz[ang], 0.0f}, ff_mul(zcn, dnv));
-        const ff r = ff_add(fst, ff_mul(tau, kafe_f));
-        const ff iD = ff_recip(ff_add(ff{1.0f, 0.0f}, ff_mul(kt_f, tau)));
+        ff p = ff_mul_f(zcn, dnv);
+        if (ang == cat) p = ff_add(p, ff_mul(zcn, cval_f));
+        const ff fst = ff_add(p, fzv);
+        const ff iD = ff_recip(ff_add(ff_mul(kt_f, tau), 1.0f));
         buf[4 * ang] = fst.hi; buf[4 * ang + 1] = fst.lo;
         buf[4 * ang + 2] = iD.hi; buf[4 * ang + 3] = iD.lo;
-        const ff domD = ff_mul(dom, iD);
-        sr = ff_add(sr, ff_mul(domD, r));
-        s1 = ff_add(s1, ff_mul(domD, ff_add(ff{1.0f, 0.0f}, ff_mul(ka_f, tau))));
+        const ff w = ff_mul(dom, iD);
+        sA = ff_add(sA, ff_mul(w, fst));
+        sB = ff_add(sB, ff_mul(w, tau));
+        sC = ff_add(sC, w);
+      };
+      // two angles a lane per pass, both loaded first (in ascending order)
+      for (int a0 = lane; a0 < NA; a0 += 64) {
+        const int a1 = a0 + 32;
+        const bool has1 = a1 < NA;
+        const float d0 = (float)dn[a0], f0 = (float)fz[a0];
+        const float d1 = has1 ? (float)dn[a1] : 0.0f, f1 = has1 ? (float)fz[a1] : 0.0f;
+        bin1(a0, d0, f0);
+        if (has1) bin1(a1, d1, f1);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        sr = ff_add(sr, ff_shfl_xor(sr, o));
-        s1 = ff_add(s1, ff_shfl_xor(s1, o));
+        sA = ff_add(sA, ff_shfl_xor(sA, o));
+        sB = ff_add(sB, ff_shfl_xor(sB, o));
+        sC = ff_add(sC, ff_shfl_xor(sC, o));
       }
+      const ff sr = ff_add(sA, ff_mul(kafe_f, sB));
+      const ff s1 = ff_add(sC, ff_mul(ka_f, sB));
       const ff J = ff_mul(sr, ff_recip(s1));
-      const ff ksJ = ff_mul(ks_f, J);
+      // f = (f* + tau (ka fe + ks J)) / D
+      const ff gJ = ff_add(kafe_f, ff_mul(ks_f, J));
       // number and momentum weights of the row; energy is eps_i times them
       float fN = 0.0f, fP0 = 0.0f, fP1 = 0.0f, fP2 = 0.0f;
       const float eps_i = (float)S.epsS[i];
@@ -1951,12 +1996,11 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         const ff tau = S.zt_f[ang];
         const ff fst = ff{buf[4 * ang], buf[4 * ang + 1]};
         const ff iD = ff{buf[4 * ang + 2], buf[4 * ang + 3]};
-        const ff r = ff_add(fst, ff_mul(tau, kafe_f));
-        const ff fn = ff_mul(ff_add(r, ff_mul(tau, ksJ)), iD);
+        const ff fn = ff_mul(ff_add(fst, ff_mul(tau, gJ)), iD);
         const float fw = fn.hi + fn.lo;
         fo[ang] = fw;
         bad |= !isfinite(fw);
-        const ff del = ff_add(ff{fw, 0.0f}, ff_neg(fst));
+        const ff del = ff_add(ff_neg(fst), fw);
         const float dc = S.zq_f[ang] * dg_i * (del.hi + del.lo);
         fN += dc;
         fP0 += dc * (float)S.n0[ang];
@@ -2889,12 +2933,14 @@ int launch_zone_t(const Tables& tb, const State& st, double dt, void* dep, void*
   T* d = reinterpret_cast<T*>(dep);
   DepRec* r = reinterpret_cast<DepRec*>(rec);
   if constexpr (sizeof(T) == 4) {
-    // two of the benchmark configurations' grids at compile time (as the
-    // face pass; for 20 groups x 128 angles the specialised zone pass spills
-    // and was slower, 19.1 -> 19.3 ms)
+    // the benchmark configurations' grids at compile time (as the face pass)
     auto grid_is = [&](int ne, int na, int nmu, int nph) {
       return tb.n_e == ne && tb.n_ang == na && tb.n_mu == nmu && tb.n_ph == nph;
     };
+    if (grid_is(20, 128, 16, 8)) {
+      k_zone_collide<T, 20, 128, 16, 8><<<grid, 256, sm2, s>>>(tb, st, dt, d, r);
+      return (int)cudaGetLastError();
+    }
     if (grid_is(12, 80, 8, 10)) {
       k_zone_collide<T, 12, 80, 8, 10><<<grid, 256, sm2, s>>>(tb, st, dt, d, r);
       return (int)cudaGetLastError();
@@ -3010,6 +3056,7 @@ int prepare_kernels() {
   BT_SET((k_flux_faces<double, 512, 5>));
   BT_SET((k_zone_collide<float>));
   BT_SET((k_zone_collide<float, 12, 80, 8, 10>));
+  BT_SET((k_zone_collide<float, 20, 128, 16, 8>));
   BT_SET((k_zone_collide<float, 8, 48, 6, 8>));
   BT_SET((k_zone_collide<double>));
   BT_SET((k_time_remap<float, 128>));
