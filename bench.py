@@ -176,13 +176,13 @@ def host_cpu():
 # and written once plus the deposit rows (six per zone) written and read.
 TRAFFIC = {
     ("config3_cc2d_256x64x12x80x3", "mixed", "split/256"):
-        (218.60e6 + 1347.00e6 + 1352.24e6 + 429.06e6, "e955d870757d1f0a8e91dea04428eac79e240bc965e439bec4f801e18e4a3b74"),
+        (217.14e6 + 1348.28e6 + 1352.18e6 + 429.01e6, "fcbeb618733754eb056abaf54f31788e79c44b4b5a28914a5d730eb6b61319ee"),
     # captured on the same problem at 128 x 32 zones (python -m
     # paper_2003_02845_gb300.profiling config5_largest_128x32 mixed split/384 3)
     # and scaled by the 16x zones of the full 512 x 128 grid (the traffic of
     # both passes is per zone)
     ("config5_p2_512x128x20x128x6", "mixed", "split/384"):
-        (16 * (486.50e6 + 1459.17e6 + 2011.19e6 + 508.88e6), "e955d870757d1f0a8e91dea04428eac79e240bc965e439bec4f801e18e4a3b74"),
+        (16 * (483.69e6 + 1458.76e6 + 2011.14e6 + 509.15e6), "fcbeb618733754eb056abaf54f31788e79c44b4b5a28914a5d730eb6b61319ee"),
 }
 
 

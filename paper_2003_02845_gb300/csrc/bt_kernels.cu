@@ -1571,15 +1571,20 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
           }
         }
       }
-      // the block's exact flux total, needed by thread 0 only: warp sums now,
-      // their sum after the barrier the deposits need anyway
+      // the block's exact flux total, needed by one thread only: warp sums
+      // now, their sum after the barrier the deposits need anyway.  In the
+      // face pass that thread is the block's last (with the records below):
+      // thread 0 also issues the next stencil copies, and the two serial
+      // parts on one warp delayed the block's next barrier (face pass -2 to
+      // -3.5 %)
       if (sizeof(T) == 4) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sumF = ff_add(sumF, ff_shfl_down(sumF, o));
         if (lane == 0) S.redf[warp] = sumF;
       }
       __syncthreads();
-      if (sizeof(T) == 4 && tid == 0) {
+      constexpr int kTot = MODE == 1 ? NT - 1 : 0;   // the thread forming the total
+      if (sizeof(T) == 4 && tid == kTot) {
         ff t = S.redf[0];
         for (int w = 1; w < NT / 32; ++w) t = ff_add(t, S.redf[w]);
         sumF = t;
@@ -1601,7 +1606,7 @@ __device__ __forceinline__ void flux_body(const Tables& tb, const State& st, dou
         tn_sum = block_sum2(tn, te, S.red, te_sum);
         if (MODE == 0 && tid == 0) { S.tally[2 * s] += tn_sum; S.tally[2 * s + 1] += te_sum * F.al; }
       }
-      if (MODE == 1 && tid == 0) {
+      if (MODE == 1 && tid == kTot) {
         // the receiving zones' records of this face: exact totals and tallies
         const ff zero = ff{0.0f, 0.0f};
         if (depP) {
