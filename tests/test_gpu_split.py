@@ -97,10 +97,11 @@ def test_autotune_considers_split(gpu, tmp_path, monkeypatch):
     t.step(0.01)   # the chosen shape runs
 
 
-# The face pass has instantiations for the benchmark configurations' grids
-# (groups, mu cells and Phi cells fixed at compile time, float32).  On small
-# spatial grids with those momentum grids, the specialised face pass must
-# give bit for bit what the generic fused kernel gives.
+# The face and zone passes have instantiations for the benchmark
+# configurations' grids (groups, mu cells and Phi cells fixed at compile
+# time, float32; the zone pass's with paired loads).  On small spatial grids
+# with those momentum grids, the specialised passes must give bit for bit
+# what the generic fused kernel gives.
 @pytest.mark.parametrize("n_e,n_mu,n_phi,shape", [(20, 16, 8, SPLIT | 512), (20, 16, 8, SPLIT | 384),
                                                   (12, 8, 10, SPLIT | 256), (8, 6, 8, SPLIT | 256)])
 def test_specialised_grids_equal_fused(gpu, n_e, n_mu, n_phi, shape):
